@@ -1,0 +1,336 @@
+"""Seeded synthetic inputs for the rollout planner: terrain heightmaps, vehicles,
+initial states and candidate control sequences.
+
+This module produces input data only.  It holds none of the planner's
+arithmetic (no vehicle dynamics, no terrain lookup, no constraint or cost), so
+the FP64 oracle and the CUDA path can both consume its output without sharing
+any code of the method.
+
+Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) turned into uniforms on (0, 1)
+and normals by the Box-Muller transform, all in FP64 numpy, so the same seed
+gives the same bytes on any host.
+
+The terrain shapes stand in for the paper's private photogrammetric scan of a
+hilly off-road park (Sec. V-A: rough trails with bumps, ruts, berms and
+banked turns).  The paper's scan, obstacle polygons and plant are not
+available, so every workload here is synthetic.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def splitmix64(seed: int, stream: int, n: int) -> np.ndarray:
+    """n SplitMix64 outputs of the generator seeded by (seed, stream)."""
+    with np.errstate(over="ignore"):
+        base = _mix(np.array([(seed * 0x100000001B3 + stream) & 0xFFFFFFFFFFFFFFFF],
+                             dtype=np.uint64))[0]
+        ctr = np.arange(1, n + 1, dtype=np.uint64) * _GOLDEN + base
+        return _mix(ctr)
+
+
+def uniform(seed: int, stream: int, n: int) -> np.ndarray:
+    """n uniforms on the open interval (0, 1), FP64."""
+    bits = splitmix64(seed, stream, n) >> np.uint64(11)
+    return (bits.astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def normal(seed: int, stream: int, n: int) -> np.ndarray:
+    """n standard normals by Box-Muller, FP64."""
+    m = (n + 1) // 2
+    u = uniform(seed, stream, 2 * m)
+    r = np.sqrt(-2.0 * np.log(u[:m]))
+    t = 2.0 * math.pi * u[m:]
+    return np.concatenate([r * np.cos(t), r * np.sin(t)])[:n]
+
+
+# ----------------------------------------------------------------------------
+# Vehicles (SI units).  Keys follow the paper's notation table (App. A):
+# M, J, L_f, L_r, e (track), h+R (CoM height over the contact patch), k, b,
+# tire C and mu, delta_max, delta_rate_max, g.
+# ----------------------------------------------------------------------------
+
+def vehicle_mrzr() -> dict:
+    """Polaris MRZR D4 of the paper's model and simulation-tire parameter tables (App. B)."""
+    return dict(M=969.0, Jxx=280.9, Jyy=692.1, Jzz=810.7, Lf=1.565, Lr=1.148,
+                e=1.280, hR=0.380 + 0.291, kf=4.2e4, kr=5.8e4, bf=3.1e3, br=4.3e3,
+                C=6.1, mu=0.6, delta_max=0.639, delta_rate_max=1.0, g=9.81)
+
+
+def vehicle_baseline() -> dict:
+    """The 1000 kg benchmark vehicle: wheelbase 2.5 m, track 1.5 m, CoM height
+    0.6 m, 40 kN/m spring and 3 kN s/m damper at every corner.  What the
+    benchmark leaves open is filled from App. B: the front/rear split of the
+    wheelbase in the MRZR's ratio, the MRZR inertias, the simulation tire
+    (C = 6.1 /rad, mu = 0.6), delta_max = 0.639 rad, |delta_dot| <= 1 rad/s."""
+    L = 2.5
+    return dict(M=1000.0, Jxx=280.9, Jyy=692.1, Jzz=810.7,
+                Lf=L * 1.565 / (1.565 + 1.148), Lr=L * 1.148 / (1.565 + 1.148),
+                e=1.5, hR=0.6, kf=4.0e4, kr=4.0e4, bf=3.0e3, br=3.0e3,
+                C=6.1, mu=0.6, delta_max=0.639, delta_rate_max=1.0, g=9.81)
+
+
+def cost_default(goal_x: float, goal_y: float) -> dict:
+    """Cost weights of Sec. IV-C: w_t = 5 /s, w_c = 8 /s per (rad/s)^2,
+    w_g = 15 /m, sigma = 1e6 /s, goal radius 2.5 m.  eps_esm = 0 asks each
+    side for its default, 10 % of the level-ground energy stability margin."""
+    return dict(wt=5.0, wc=8.0, wg=15.0, sigma=1.0e6, eps_esm=0.0,
+                goal_x=float(goal_x), goal_y=float(goal_y), goal_r=2.5)
+
+
+# ----------------------------------------------------------------------------
+# Terrain
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Terrain:
+    """Row-major heightmap: heights[j, i] = f(x0 + i*cell, y0 + j*cell)."""
+    heights: np.ndarray            # float32 [ny, nx]
+    cell: float
+    x0: float = 0.0
+    y0: float = 0.0
+    costmap: np.ndarray | None = None   # float32 [ny, nx] or None
+    name: str = ""
+
+    @property
+    def nx(self) -> int:
+        return int(self.heights.shape[1])
+
+    @property
+    def ny(self) -> int:
+        return int(self.heights.shape[0])
+
+    def grid(self):
+        xs = self.x0 + self.cell * np.arange(self.nx, dtype=np.float64)
+        ys = self.y0 + self.cell * np.arange(self.ny, dtype=np.float64)
+        return np.meshgrid(xs, ys)
+
+
+def _smoothstep(t):
+    t = np.clip(t, 0.0, 1.0)
+    return t * t * (3.0 - 2.0 * t)
+
+
+def fbm(n: int, cell: float, amplitude: float, seed: int, stream: int = 1,
+        octaves: int = 5, dirs: int = 8, lambda0: float = 12.8) -> np.ndarray:
+    """Spectral fractional-Brownian-motion-like field on an n x n grid (FP64).
+
+    Octave o sums `dirs` plane waves with random directions and phases,
+    wavelength lambda0 / 2**o and gain 0.5**o; the field is then scaled so
+    that max |f| = amplitude."""
+    u = uniform(seed, stream, octaves * dirs * 2)
+    ang = 2.0 * math.pi * u[: octaves * dirs]
+    phs = 2.0 * math.pi * u[octaves * dirs:]
+    c = cell * np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(c, c)
+    f = np.zeros((n, n))
+    for o in range(octaves):
+        lam = lambda0 / 2.0 ** o
+        g = 0.5 ** o
+        for d in range(dirs):
+            a = ang[o * dirs + d]
+            p = phs[o * dirs + d]
+            f += g * np.cos((2.0 * math.pi / lam) * (X * math.cos(a) + Y * math.sin(a)) + p)
+    return f * (amplitude / np.max(np.abs(f)))
+
+
+def _raised_cosine(s, height, base):
+    half = 0.5 * base
+    return np.where(np.abs(s) < half, height * 0.5 * (1.0 + np.cos(math.pi * s / half)), 0.0)
+
+
+def terrain_plain(seed: int = 0) -> Terrain:
+    """256 x 256 at 0.2 m: fBm (5 octaves, 0.5 m), two 0.4 m berms crossing
+    the path obliquely at x = 9 m and 13 m, one 15 degree side slope over
+    x in [15, 23] m blended in over 2 m."""
+    n, cell = 256, 0.2
+    f = fbm(n, cell, 0.5, seed, stream=11)
+    X, Y = np.meshgrid(cell * np.arange(n), cell * np.arange(n))
+    yc = 25.6
+    for xc, deg in ((9.0, 30.0), (13.0, -30.0)):
+        a = math.radians(deg)
+        s = (X - xc) * math.cos(a) - (Y - yc) * math.sin(a)
+        f += _raised_cosine(s, 0.4, 1.5)
+    w = _smoothstep((X - 13.0) / 2.0) * _smoothstep((25.0 - X) / 2.0)
+    f += w * math.tan(math.radians(15.0)) * (Y - yc)
+    return Terrain(f.astype(np.float32), cell, name="plain-256-0.2m")
+
+
+def terrain_scaled(seed: int = 0, n: int = 1024, cell: float = 0.1) -> Terrain:
+    """1024 x 1024 at 0.1 m: fBm (0.8 m), two 0.3 m deep, 0.3 m wide ruts
+    1.5 m apart running along x with a 0.5 m sinusoidal wander, and side
+    slopes alternating +/-20 degrees in 8 m segments along x, blended over 2 m."""
+    f = fbm(n, cell, 0.8, seed, stream=12)
+    X, Y = np.meshgrid(cell * np.arange(n), cell * np.arange(n))
+    yc = 0.5 * n * cell
+    wander = 0.5 * np.sin(2.0 * math.pi * X / 17.0)
+    for off in (-0.75, 0.75):
+        f -= _raised_cosine(Y - (yc + off + wander), 0.3, 0.3)
+    seg = 8.0
+    b = np.round(X / seg)                       # nearest segment boundary
+    d = X - b * seg                             # signed distance to it, [-4, 4]
+    right = np.where((b % 2) == 0, 1.0, -1.0)   # sign of the segment after it
+    s = -right + 2.0 * right * _smoothstep((d + 1.0) / 2.0)   # 2 m blend
+    f += s * math.tan(math.radians(20.0)) * (Y - yc)
+    return Terrain(f.astype(np.float32), cell, name=f"scaled-{n}-{cell}m")
+
+
+def terrain_tile(side: int, seed: int, cell: float = 0.1) -> Terrain:
+    """A serving vehicle's own tile: fBm (0.6 m) plus one 0.4 m berm and a
+    12 degree bank, side x side nodes at `cell`."""
+    f = fbm(side, cell, 0.6, seed, stream=13)
+    X, Y = np.meshgrid(cell * np.arange(side), cell * np.arange(side))
+    ext = side * cell
+    u = uniform(seed, 14, 3)
+    xc = ext * (0.3 + 0.4 * u[0])
+    a = math.radians(60.0 * (u[1] - 0.5))
+    s = (X - xc) * math.cos(a) - (Y - 0.5 * ext) * math.sin(a)
+    f += _raised_cosine(s, 0.4, 1.5)
+    f += math.tan(math.radians(12.0 * (2.0 * u[2] - 1.0))) * (Y - 0.5 * ext) * 0.3
+    return Terrain(f.astype(np.float32), cell, name=f"tile-{side}-{cell}m-s{seed}")
+
+
+def terrain_plane(nx: int, ny: int, cell: float, a: float, b: float, c: float,
+                  x0: float = 0.0, y0: float = 0.0) -> Terrain:
+    """f = a + b x + c y sampled on the grid (exact in FP32 when a, b, c, cell
+    and the origin are dyadic and the grid is small)."""
+    xs = x0 + cell * np.arange(nx)
+    ys = y0 + cell * np.arange(ny)
+    X, Y = np.meshgrid(xs, ys)
+    return Terrain((a + b * X + c * Y).astype(np.float32), cell, x0, y0, name="plane")
+
+
+# ----------------------------------------------------------------------------
+# Initial state and candidates
+# ----------------------------------------------------------------------------
+
+STATE = ("x", "y", "z", "psi", "theta", "phi", "vx", "vy", "vz", "wx", "wy", "wz", "delta")
+
+
+def settled_state(terrain: Terrain, veh: dict, x: float, y: float, psi: float,
+                  vx: float) -> np.ndarray:
+    """Chassis placed on the least-squares plane through the terrain nodes
+    nearest to its four nominal wheel positions: body z along the plane
+    normal, heading psi projected into the plane, CoM at h+R above it.
+    Rates zero, steering zero.  Returns float32 [13] in the paper's state
+    order (x, y, z, psi, theta, phi, vx, vy, vz, wx, wy, wz, delta)."""
+    cps, sps = math.cos(psi), math.sin(psi)
+    pts = []
+    for lx in (veh["Lf"], -veh["Lr"]):
+        for ly in (0.5 * veh["e"], -0.5 * veh["e"]):
+            px = x + cps * lx - sps * ly
+            py = y + sps * lx + cps * ly
+            i = int(round((px - terrain.x0) / terrain.cell))
+            j = int(round((py - terrain.y0) / terrain.cell))
+            i = min(max(i, 0), terrain.nx - 1)
+            j = min(max(j, 0), terrain.ny - 1)
+            pts.append((terrain.x0 + i * terrain.cell, terrain.y0 + j * terrain.cell,
+                        float(terrain.heights[j, i])))
+    P = np.array(pts)
+    A = np.stack([np.ones(4), P[:, 0], P[:, 1]], axis=1)
+    (a, b, c), *_ = np.linalg.lstsq(A, P[:, 2], rcond=None)
+    n = np.array([-b, -c, 1.0])
+    n /= np.linalg.norm(n)
+    hx = np.array([cps, sps, 0.0])
+    bx = hx - np.dot(hx, n) * n
+    bx /= np.linalg.norm(bx)
+    by = np.cross(n, bx)
+    Rm = np.stack([bx, by, n], axis=1)           # columns = body axes in world
+    theta = -math.asin(max(-1.0, min(1.0, Rm[2, 0])))
+    phi = math.atan2(Rm[2, 1], Rm[2, 2])
+    yaw = math.atan2(Rm[1, 0], Rm[0, 0])
+    # CoM so that the plane point below it, along n, is h+R away
+    z = (a + b * (x - veh["hR"] * n[0]) + c * (y - veh["hR"] * n[1])) + veh["hR"] * n[2]
+    s = np.zeros(13)
+    s[0], s[1], s[2] = x, y, z
+    s[3], s[4], s[5] = yaw, theta, phi
+    s[6] = vx
+    return s.astype(np.float32)
+
+
+def candidates(N: int, H: int, seed: int, sigma_rate: float = 0.2,
+               sigma_acc: float = 0.3, nominal=(0.0, 0.0)) -> np.ndarray:
+    """Candidate controls zeta = (steering rate [rad/s], longitudinal
+    acceleration [m/s^2]) held per control step, float32 [H, N, 2]
+    (time-major).  Candidate 0 is the unperturbed nominal; the others are
+    i.i.d. normal perturbations about it."""
+    u = np.empty((H, N, 2), dtype=np.float64)
+    u[..., 0] = nominal[0] + sigma_rate * normal(seed, 21, H * N).reshape(H, N)
+    u[..., 1] = nominal[1] + sigma_acc * normal(seed, 22, H * N).reshape(H, N)
+    u[:, 0, 0] = nominal[0]
+    u[:, 0, 1] = nominal[1]
+    return u.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    terrain: Terrain
+    vehicle: dict
+    cost: dict
+    x0: np.ndarray                  # float32 [13] (shared) or [N, 13]
+    ctrl: np.ndarray                # float32 [H, N, 2]
+    dt: float
+    n_sub: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return int(self.ctrl.shape[1])
+
+    @property
+    def H(self) -> int:
+        return int(self.ctrl.shape[0])
+
+
+def workload_plain(seed: int = 0, N: int = 1024, H: int = 40, dt: float = 0.05,
+                   goal=(45.0, 25.6)) -> Workload:
+    """Plain single plan: 1024 candidates, horizon 40 at dt = 0.05 s (10 Euler
+    substeps of 5 ms), 8 m/s straight nominal from (5, 25.6) on the 256^2
+    terrain; steering-rate sigma 0.2 rad/s, acceleration sigma 0.3 m/s^2."""
+    ter = terrain_plain(seed)
+    veh = vehicle_baseline()
+    x0 = settled_state(ter, veh, 5.0, 25.6, 0.0, 8.0)
+    ctrl = candidates(N, H, seed)
+    return Workload("plain-1024x40", ter, veh, cost_default(*goal), x0, ctrl, dt,
+                    n_sub=max(1, math.ceil(round(dt / 0.005, 9))),
+                    meta=dict(seed=seed))
+
+
+def workload_scaled(seed: int = 0, N: int = 16384, H: int = 100, dt: float = 0.02,
+                    terrain: Terrain | None = None) -> Workload:
+    """Scaled rollout: 16384 candidates, horizon 100 at dt = 0.02 s (4
+    substeps), per-candidate initial speed uniform in [5, 15] m/s, from
+    (10, 51.2) on the 1024^2 terrain at 0.1 m."""
+    ter = terrain if terrain is not None else terrain_scaled(seed)
+    veh = vehicle_baseline()
+    base = settled_state(ter, veh, 10.0, 51.2, 0.0, 10.0)
+    x0 = np.repeat(base[None, :], N, axis=0)
+    x0[:, 6] = (5.0 + 10.0 * uniform(seed, 31, N)).astype(np.float32)
+    ctrl = candidates(N, H, seed)
+    return Workload(f"scaled-{N}x{H}", ter, veh, cost_default(95.0, 51.2), x0, ctrl, dt,
+                    n_sub=max(1, math.ceil(round(dt / 0.005, 9))),
+                    meta=dict(seed=seed))
+
+
+def n_substeps(dt: float, h_max: float = 0.005) -> int:
+    """Euler substeps per control step: ceil(dt / 5 ms)."""
+    return max(1, math.ceil(round(dt / h_max, 9)))

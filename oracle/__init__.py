@@ -1,0 +1,220 @@
+"""FP64 CPU oracle of the SRB rollout planner (arxiv 2603.20525, Sec. IV).
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It is an
+independent restatement of the paper in plain C (``srb.c``), built with gcc
+into ``oracle/_build/liboracle.so`` and called through ctypes.  It shares no
+code with the CUDA path, and the product never falls back to it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = [os.path.join(_HERE, "srb.c")]
+_HDR = [os.path.join(_HERE, "oracle.h")]
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
+WHEEL_FIELDS = ("Px", "Py", "Pz", "vix", "viy", "viz", "f", "fx", "fy", "cmap",
+                "taux", "tauy", "tauz", "chi", "chidot", "Fk", "Fb", "Fz", "alpha",
+                "Fy", "Fx", "offmap")
+BODY_FIELDS = tuple(f"R{i}" for i in range(9)) + ("gBx", "gBy", "gBz", "Fy", "Fz",
+                                                 "Mx", "My", "Mz", "U", "L",
+                                                 "Fs_fl", "Fs_fr", "Fs_rl", "Fs_rr")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (FP64, no FMA contraction, OpenMP)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _SRC + _HDR)
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= newest:
+        return _OUT
+    tmp = _OUT + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
+           "-fno-fast-math", "-fPIC", "-shared", "-fopenmp", "-Wall", "-Wno-unknown-pragmas",
+           *_SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    os.replace(tmp, _OUT)
+    return _OUT
+
+
+class Vehicle(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("M", "Jxx", "Jyy", "Jzz", "Lf", "Lr", "e", "hR",
+                                          "kf", "kr", "bf", "br", "C", "mu", "delta_max",
+                                          "delta_rate_max", "g")]
+
+
+class Cost(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("wt", "wc", "wg", "sigma", "eps_esm",
+                                          "goal_x", "goal_y", "goal_r")]
+
+
+class _Terrain(C.Structure):
+    _fields_ = [("heights", C.POINTER(C.c_float)), ("gx", C.POINTER(C.c_double)),
+                ("gy", C.POINTER(C.c_double)), ("costmap", C.POINTER(C.c_float)),
+                ("nx", C.c_int), ("ny", C.c_int), ("cell", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double)]
+
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_up = C.POINTER(C.c_ubyte)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_terrain_gradients.argtypes = [_fp, C.c_int, C.c_int, C.c_double, _dp, _dp]
+            L.orc_terrain_sample.argtypes = [C.POINTER(_Terrain), C.c_double, C.c_double, _dp]
+            L.orc_terrain_sample.restype = C.c_int
+            L.orc_tire.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.orc_tire.restype = C.c_double
+            L.orc_esm.argtypes = [C.POINTER(Vehicle), C.c_double, C.c_double]
+            L.orc_esm.restype = C.c_double
+            L.orc_rotation.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+            L.orc_eval.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                   _dp, _dp, _dp, _dp, _dp]
+            L.orc_rollout.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                      _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                      _dp, _dp, _up, _dp, _dp, _dp, C.c_int]
+            L.orc_rollout.restype = C.c_int
+            L.orc_trajectory.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                         _dp, _fp, C.c_int, C.c_double, C.c_int, _dp, _dp]
+            L.orc_trajectory.restype = C.c_int
+            L.orc_select.argtypes = [_dp, _up, C.c_int]
+            L.orc_select.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def vehicle(d: dict) -> Vehicle:
+    return Vehicle(**{k: float(d[k]) for k, _ in Vehicle._fields_})
+
+
+def cost(d: dict) -> Cost:
+    return Cost(**{k: float(d[k]) for k, _ in Cost._fields_})
+
+
+class Terrain:
+    """Oracle view of a heightmap: FP32 heights (the same bytes the GPU gets),
+    FP64 node gradients computed here, optional FP32 costmap."""
+
+    def __init__(self, heights, cell, x0=0.0, y0=0.0, costmap=None):
+        self.heights = np.ascontiguousarray(heights, dtype=np.float32)
+        ny, nx = self.heights.shape
+        self.gx = np.empty((ny, nx), dtype=np.float64)
+        self.gy = np.empty((ny, nx), dtype=np.float64)
+        lib().orc_terrain_gradients(_ptr(self.heights, _fp), nx, ny, float(cell),
+                                    _ptr(self.gx, _dp), _ptr(self.gy, _dp))
+        self.costmap = None if costmap is None else np.ascontiguousarray(costmap, np.float32)
+        self.c = _Terrain(_ptr(self.heights, _fp), _ptr(self.gx, _dp), _ptr(self.gy, _dp),
+                          _ptr(self.costmap, _fp), nx, ny, float(cell), float(x0), float(y0))
+
+    @classmethod
+    def of(cls, t):
+        """From a gen.Terrain-like object (heights, cell, x0, y0, costmap)."""
+        return cls(t.heights, t.cell, t.x0, t.y0, getattr(t, "costmap", None))
+
+    def sample(self, x, y):
+        out = np.empty(4)
+        off = lib().orc_terrain_sample(C.byref(self.c), float(x), float(y), _ptr(out, _dp))
+        return out, bool(off)
+
+
+def tire(Cc, mu, alpha):
+    return lib().orc_tire(float(Cc), float(mu), float(alpha))
+
+
+def esm(veh: dict, phi, theta):
+    return lib().orc_esm(C.byref(vehicle(veh)), float(phi), float(theta))
+
+
+def rotation(psi, theta, phi):
+    R = np.empty(9)
+    lib().orc_rotation(float(psi), float(theta), float(phi), _ptr(R, _dp))
+    return R.reshape(3, 3)
+
+
+def evaluate(veh: dict, cst: dict, ter: Terrain, xi, zeta):
+    """xi_dot, per-wheel diagnostics [4, 22] and body diagnostics [23]."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    zeta = np.ascontiguousarray(zeta, dtype=np.float64)
+    xd = np.empty(13)
+    wheel = np.empty((4, len(WHEEL_FIELDS)))
+    body = np.empty(len(BODY_FIELDS))
+    lib().orc_eval(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                   _ptr(xi, _dp), _ptr(zeta, _dp), _ptr(xd, _dp), _ptr(wheel, _dp),
+                   _ptr(body, _dp))
+    return xd, wheel, body
+
+
+def rollout(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int,
+            want_xf=True, want_step_margin=False, want_diag=True, nthreads=0):
+    """Roll out every candidate.  x0 float32 [13] or [N, 13]; ctrl float32 [H, N, 2]."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
+    H, N, _ = ctrl.shape
+    per = 1 if x0.ndim == 2 else 0
+    if per:
+        assert x0.shape == (N, 13)
+    J = np.empty(N)
+    margin = np.empty(N)
+    flags = np.empty(N, dtype=np.uint8)
+    xf = np.empty((N, 13)) if want_xf else None
+    sm = np.empty((H, N)) if want_step_margin else None
+    diag = np.empty((N, 3)) if want_diag else None
+    rc = lib().orc_rollout(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                           _ptr(x0, _fp), per, _ptr(ctrl, _fp), N, H, float(dt), int(n_sub),
+                           _ptr(J, _dp), _ptr(margin, _dp), _ptr(flags, _up),
+                           _ptr(xf, _dp), _ptr(sm, _dp), _ptr(diag, _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rollout rejected its arguments")
+    return dict(J=J, margin=margin, flags=flags, xf=xf, step_margin=sm, diag=diag)
+
+
+def select(J, flags) -> int:
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    return int(lib().orc_select(_ptr(J, _dp), _ptr(flags, _up), len(J)))
+
+
+def plan(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int, nthreads=0):
+    """Rollout, empirical argmin and the best candidate's outputs."""
+    r = rollout(veh, cst, ter, x0, ctrl, dt, n_sub, want_step_margin=True, nthreads=nthreads)
+    b = select(r["J"], r["flags"])
+    ctrl = np.asarray(ctrl, dtype=np.float32)
+    best_ctrl = ctrl[:, b, :].astype(np.float64)
+    best_ctrl[:, 0] = np.clip(best_ctrl[:, 0], -veh["delta_rate_max"], veh["delta_rate_max"])
+    r.update(best=b, n_feasible=int(np.count_nonzero(r["flags"] & FEASIBLE)),
+             best_cost=float(r["J"][b]), best_margin=float(r["margin"][b]),
+             best_ctrl=best_ctrl, best_step_margin=r["step_margin"][:, b].copy())
+    return r
+
+
+def trajectory(veh: dict, cst: dict, ter: Terrain, x0, ctrl_h2, dt: float, n_sub: int):
+    """One candidate with every Euler state: states [S+1, 13], running cost
+    [S+1], Euler-step index of goal arrival (or -1)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    ctrl_h2 = np.ascontiguousarray(ctrl_h2, dtype=np.float32)
+    H = ctrl_h2.shape[0]
+    S = H * n_sub
+    states = np.empty((S + 1, 13))
+    Jrun = np.empty(S + 1)
+    ds = lib().orc_trajectory(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                              _ptr(x0, _dp), _ptr(ctrl_h2, _fp), H, float(dt), int(n_sub),
+                              _ptr(states, _dp), _ptr(Jrun, _dp))
+    return states, Jrun, int(ds)
