@@ -1,0 +1,344 @@
+"""Benchmark of the GB300 rollout planner (one JSON line on rank 0).
+
+A step is one plan: the fused sm_103a kernel rolls every candidate of the
+workload forward (SRB model, terrain, suspension, tire, ESM, cost) and reduces
+to the best feasible candidate, through the C-ABI (atp_plan).  The default
+workload is the scaled rollout: 16384 candidates, horizon 100 at dt = 0.02 s
+(4 Euler steps of 5 ms), per-candidate initial speed 5-15 m/s, on a
+1024 x 1024 heightmap at 0.1 m.
+
+  value  rollout-steps/s (candidates x control steps per second) of the whole
+         job, device-timed with CUDA events per step, L2 flushed between steps
+  e2e    the same metric with host buffers: pinned host -> device copy of the
+         step's candidates and initial states, the plan, device -> host copy
+         of the result, all inside the timed region
+  --impl reference   the FP64 CPU oracle on the same workload (host cores)
+
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (weak scaling, no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic FP32 work of one Euler step of one candidate, counted from the
+# model's equations (FMA = 2 flops): rotation 20, ESM 6, goal test 5, gravity 3,
+# four wheels 4 x 107, force and moment sums 30, running cost 14, state
+# derivative 49, Euler update 26.  The 20 special functions per step (3 sincos,
+# cos(delta), 4 atan2, 4 rsqrt, 5 reciprocals) are not in the flop count.
+FLOPS_PER_SUBSTEP = 581
+SPECIAL_PER_SUBSTEP = 20
+SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops(mhz=MAX_SM_MHZ):
+    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def kernel_sources_sha256():
+    import glob
+    import hashlib
+    srcs = sorted(glob.glob(os.path.join(ROOT, "paper_2603_20525_gb300", "csrc", "*.cu")) +
+                  glob.glob(os.path.join(ROOT, "paper_2603_20525_gb300", "csrc", "*.cuh")) +
+                  [os.path.join(ROOT, "include", "atp.h")])
+    srcs = sorted(srcs, key=lambda p: os.path.relpath(p, ROOT))
+    h = hashlib.sha256()
+    for p in srcs:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources changed since the capture or it covers another workload."""
+    path = os.path.join(ROOT, "profiles", "plan_kernel_traffic.txt")
+    try:
+        kv = dict(l.split(":", 1) for l in open(path) if ":" in l and not l.startswith("#"))
+    except OSError:
+        return None
+    kv = {k.strip(): v.strip() for k, v in kv.items()}
+    if kv.get("sources_sha256") != kernel_sources_sha256() or kv.get("workload") != workload:
+        return None
+    return int(kv["dram_bytes_per_launch"])
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.index), "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm),
+                    reasons=sorted(reasons))
+
+
+def make_workload(name):
+    import gen
+    if name == "scaled":
+        return gen.workload_scaled(0)
+    if name == "plain":
+        return gen.workload_plain(0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w, name):
+    return {"workload": f"{name}: {w.N} candidates x H={w.H} at dt={w.dt} s "
+                        f"({w.n_sub} Euler steps of {1000 * w.dt / w.n_sub:g} ms), "
+                        f"{w.terrain.nx}x{w.terrain.ny} heightmap at {w.terrain.cell} m",
+            "candidates": w.N, "horizon": w.H, "dt": w.dt, "n_sub": w.n_sub,
+            "terrain": [w.terrain.ny, w.terrain.nx], "cell_m": w.terrain.cell,
+            "vehicle": "1000 kg, wheelbase 2.5 m, track 1.5 m, CoM 0.6 m, 40 kN/m, 3 kN s/m",
+            "l2": "flushed between steps (256 MB write)"}
+
+
+def run_reference(args, w, name):
+    """The FP64 CPU oracle, as it stands, on the same workload."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    t = oracle.Terrain.of(w.terrain)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.plan(w.vehicle, w.cost, t, w.x0, w.ctrl, w.dt, w.n_sub)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.plan(w.vehicle, w.cost, t, w.x0, w.ctrl, w.dt, w.n_sub)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = w.N * w.H / (ms / 1000)
+    unit = "rollout-steps/s"
+    print(json.dumps({
+        "impl": "reference", "metric": "rollout-steps/s", "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, name),
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": f"the full {name} workload per step, FP64 C oracle, OpenMP over candidates"},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "substeps_per_s": value * w.n_sub,
+    }), flush=True)
+
+
+def cpu_baseline(w, budget_s=10.0):
+    """The oracle on a bounded sample: whole plans of the workload repeated
+    for about budget_s seconds on every host core."""
+    import oracle
+    t = oracle.Terrain.of(w.terrain)
+    oracle.plan(w.vehicle, w.cost, t, w.x0, w.ctrl, w.dt, w.n_sub)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.plan(w.vehicle, w.cost, t, w.x0, w.ctrl, w.dt, w.n_sub)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 200:
+            break
+    return {"value": n * w.N * w.H / el, "unit": "rollout-steps/s", "cores": os.cpu_count() or 1,
+            "kind": "oracle",
+            "sample": f"{n} whole plans of the workload ({n * w.N} candidates, {el:.1f} s), FP64"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scaled", choices=["scaled", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = make_workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w, args.workload)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2603_20525_gb300 import atp
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    ctx = atp.Context(local)
+    ctx.reserve(w.N, w.H)
+    heights = torch.as_tensor(w.terrain.heights).to(dev)
+    ter = ctx.terrain_prepare(heights, w.terrain.cell, w.terrain.x0, w.terrain.y0)
+    ctrl = torch.as_tensor(w.ctrl).to(dev)
+    per = w.x0.ndim == 2
+    x0 = torch.as_tensor(np.ascontiguousarray(w.x0.T)).to(dev) if per else [float(v) for v in w.x0]
+    outs = ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, out=outs)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    for i in range(args.steps):
+        flush.zero_()                       # evict L2 between steps
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(per_step)
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = w.N * w.H
+    value = ws * units / (ms / 1000)
+
+    # end to end through the public API with host buffers
+    ctrl_h = torch.as_tensor(w.ctrl).pin_memory()
+    x0_h = torch.as_tensor(np.ascontiguousarray(w.x0.T)).pin_memory() if per else None
+    ctrl_d = torch.empty_like(ctrl)
+    x0_d = torch.empty_like(x0) if per else None
+    res_h = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in outs.items()}
+
+    def e2e_step():
+        ctrl_d.copy_(ctrl_h, non_blocking=True)
+        if per:
+            x0_d.copy_(x0_h, non_blocking=True)
+        o = ctx.plan(w.vehicle, w.cost, ter, x0_d if per else x0, ctrl_d, w.dt, w.n_sub, out=outs)
+        for k, v in o.items():
+            res_h[k].copy_(v, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ee[i][0].record(stream)
+        e2e_step()
+        ee[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in ee)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = ctrl_h.numel() * 4 + (x0_h.numel() * 4 if per else 0)
+    d2h = sum(v.numel() * v.element_size() for v in res_h.values())
+
+    if rank == 0:
+        substeps = units * w.n_sub
+        achieved = FLOPS_PER_SUBSTEP * substeps / (ms / 1000) / 1e12
+        peak = fp32_peak_tflops()
+        line = {
+            "metric": "rollout-steps/s", "value": value, "unit": "rollout-steps/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(w, args.workload),
+            "substeps_per_s": value * w.n_sub,
+            "latency_ms": {"p50": float(np.percentile(per_step, 50)),
+                           "p99": float(np.percentile(per_step, 99))},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                         "kernel": "plan_kernel (fused rollout + argmin)",
+                         "note": f"{FLOPS_PER_SUBSTEP} algorithmic FP32 flops per Euler step x "
+                                 f"{substeps} Euler steps per launch; peak = 152 SMs x 128 FP32 "
+                                 f"lanes x 2 x 2070 MHz (derived)"},
+            "e2e": {"value": ws * units / (e2e_ms / 1000), "unit": "rollout-steps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -22,6 +22,7 @@ import math
 from dataclasses import dataclass, field
 
 import numpy as np
+from scipy.ndimage import gaussian_filter
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 _M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -148,15 +149,24 @@ def fbm(n: int, cell: float, amplitude: float, seed: int, stream: int = 1,
     return f * (amplitude / np.max(np.abs(f)))
 
 
+def srb_lod(f: np.ndarray, cell: float, sigma_m: float = 0.3) -> np.ndarray:
+    """The single-rigid-body level of detail of Sec. V-B: the raw terrain
+    smoothed by a Gaussian of 0.3 m standard deviation, so that it is planar
+    at the length scale of a wheel as the model assumes."""
+    if sigma_m <= 0:
+        return f
+    return gaussian_filter(f, sigma=sigma_m / cell, mode="nearest")
+
+
 def _raised_cosine(s, height, base):
     half = 0.5 * base
     return np.where(np.abs(s) < half, height * 0.5 * (1.0 + np.cos(math.pi * s / half)), 0.0)
 
 
-def terrain_plain(seed: int = 0) -> Terrain:
+def terrain_plain(seed: int = 0, lod_sigma: float = 0.3) -> Terrain:
     """256 x 256 at 0.2 m: fBm (5 octaves, 0.5 m), two 0.4 m berms crossing
     the path obliquely at x = 9 m and 13 m, one 15 degree side slope over
-    x in [15, 23] m blended in over 2 m."""
+    x in [15, 23] m blended in over 2 m; then the SRB level of detail."""
     n, cell = 256, 0.2
     f = fbm(n, cell, 0.5, seed, stream=11)
     X, Y = np.meshgrid(cell * np.arange(n), cell * np.arange(n))
@@ -167,13 +177,15 @@ def terrain_plain(seed: int = 0) -> Terrain:
         f += _raised_cosine(s, 0.4, 1.5)
     w = _smoothstep((X - 13.0) / 2.0) * _smoothstep((25.0 - X) / 2.0)
     f += w * math.tan(math.radians(15.0)) * (Y - yc)
-    return Terrain(f.astype(np.float32), cell, name="plain-256-0.2m")
+    return Terrain(srb_lod(f, cell, lod_sigma).astype(np.float32), cell, name="plain-256-0.2m")
 
 
-def terrain_scaled(seed: int = 0, n: int = 1024, cell: float = 0.1) -> Terrain:
+def terrain_scaled(seed: int = 0, n: int = 1024, cell: float = 0.1,
+                   lod_sigma: float = 0.3) -> Terrain:
     """1024 x 1024 at 0.1 m: fBm (0.8 m), two 0.3 m deep, 0.3 m wide ruts
     1.5 m apart running along x with a 0.5 m sinusoidal wander, and side
-    slopes alternating +/-20 degrees in 8 m segments along x, blended over 2 m."""
+    slopes alternating +/-20 degrees in 8 m segments along x, blended over 2 m;
+    then the SRB level of detail."""
     f = fbm(n, cell, 0.8, seed, stream=12)
     X, Y = np.meshgrid(cell * np.arange(n), cell * np.arange(n))
     yc = 0.5 * n * cell
@@ -186,12 +198,13 @@ def terrain_scaled(seed: int = 0, n: int = 1024, cell: float = 0.1) -> Terrain:
     right = np.where((b % 2) == 0, 1.0, -1.0)   # sign of the segment after it
     s = -right + 2.0 * right * _smoothstep((d + 1.0) / 2.0)   # 2 m blend
     f += s * math.tan(math.radians(20.0)) * (Y - yc)
-    return Terrain(f.astype(np.float32), cell, name=f"scaled-{n}-{cell}m")
+    return Terrain(srb_lod(f, cell, lod_sigma).astype(np.float32), cell,
+                   name=f"scaled-{n}-{cell}m")
 
 
-def terrain_tile(side: int, seed: int, cell: float = 0.1) -> Terrain:
+def terrain_tile(side: int, seed: int, cell: float = 0.1, lod_sigma: float = 0.3) -> Terrain:
     """A serving vehicle's own tile: fBm (0.6 m) plus one 0.4 m berm and a
-    12 degree bank, side x side nodes at `cell`."""
+    12 degree bank, side x side nodes at `cell`; then the SRB level of detail."""
     f = fbm(side, cell, 0.6, seed, stream=13)
     X, Y = np.meshgrid(cell * np.arange(side), cell * np.arange(side))
     ext = side * cell
@@ -201,7 +214,8 @@ def terrain_tile(side: int, seed: int, cell: float = 0.1) -> Terrain:
     s = (X - xc) * math.cos(a) - (Y - 0.5 * ext) * math.sin(a)
     f += _raised_cosine(s, 0.4, 1.5)
     f += math.tan(math.radians(12.0 * (2.0 * u[2] - 1.0))) * (Y - 0.5 * ext) * 0.3
-    return Terrain(f.astype(np.float32), cell, name=f"tile-{side}-{cell}m-s{seed}")
+    return Terrain(srb_lod(f, cell, lod_sigma).astype(np.float32), cell,
+                   name=f"tile-{side}-{cell}m-s{seed}")
 
 
 def terrain_plane(nx: int, ny: int, cell: float, a: float, b: float, c: float,

@@ -1,0 +1,198 @@
+/*
+ * atp.h - C-ABI of the GB300 (sm_103a) all-terrain rollout planner.
+ *
+ * The library runs the sampling MPC hot path of arxiv 2603.20525 ("High-Speed,
+ * All-Terrain Autonomy: Ensuring Safety at the Limits of Mobility"):
+ * N candidate control sequences are rolled forward through the paper's
+ * single-rigid-body (SRB) vehicle model on a heightmap (Sec. IV-A), scored
+ * with the cost of Sec. IV-C including the energy-stability-margin (ESM) soft
+ * constraint of Sec. IV-B, and reduced to the best feasible candidate, the
+ * "empirical argmin" of Sec. IV-D.  Every step runs in the library's own CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions
+ *   - Frames (App. A): W is world-fixed with w_z up; B is body-fixed with
+ *     b_x forward, b_y left, b_z up.  SI units, angles in radians.
+ *   - State (Sec. IV-A), 13 floats in this order:
+ *       x, y, z, psi, theta, phi (3-2-1 yaw, pitch, roll), v_Bx, v_By, v_Bz,
+ *       w_Bx, w_By, w_Bz, delta (steering angle).
+ *   - Control (Sec. III-A, IV-A): zeta = (steering rate [rad/s],
+ *     longitudinal velocity rate [m/s^2]), held for dt (zero-order hold,
+ *     Sec. IV-C).  Candidates are float2 ctrl[H][N], time-major, so one
+ *     control step of a warp's 32 candidates is 256 contiguous bytes.
+ *   - Heights: heights[j][i] = f(x0 + i*cell, y0 + j*cell), row-major FP32.
+ *   - Each control step runs n_sub forward-Euler steps of h = dt / n_sub
+ *     (n_sub = 0 selects ceil(dt / 5 ms), the paper's 5 ms step, Sec. IV-D).
+ *
+ * Ownership and asynchrony
+ *   All array arguments named *_dev are device pointers owned by the caller.
+ *   Structs passed by pointer without _dev are host memory read during the
+ *   call only.  Every compute call is enqueued on the given stream (NULL =
+ *   legacy default stream) and returns before the GPU finishes; outputs are
+ *   valid once the stream has been synchronized.  A context owns only small
+ *   scratch buffers (the reduction key, counters and, when the caller does not
+ *   supply them, per-candidate outputs), is bound to one device, and is not
+ *   thread-safe: use one context per host thread or stream, because calls on
+ *   one context that overlap on the GPU share its scratch.
+ *
+ * Errors
+ *   Every int-returning call returns ATP_OK (0) or a negative ATP_ERR_* code
+ *   and never throws.  atp_last_error() gives a one-line reason.  Invalid
+ *   arguments are rejected before anything is enqueued.  A candidate whose
+ *   rollout turns non-finite is data, not an error: its cost is +inf and it
+ *   is infeasible, with ATP_FLAG_NONFINITE set.
+ */
+#ifndef ATP_H
+#define ATP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ATP_VERSION 1
+
+enum {
+    ATP_OK = 0,
+    ATP_ERR_INVALID = -1,     /* null pointer, bad size, non-finite parameter */
+    ATP_ERR_UNSUPPORTED = -2, /* size or format the library does not handle */
+    ATP_ERR_NOMEM = -3,       /* device allocation failed */
+    ATP_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    ATP_ERR_TIMEOUT = -5      /* a bounded device wait gave up */
+};
+
+/* texel formats of a prepared terrain */
+enum {
+    ATP_TERRAIN_F32X4 = 0,    /* float4 (f, f_x, f_y, cost) per node, 16 B */
+    ATP_TERRAIN_BF16X4 = 1    /* 4 x bf16 per node, 8 B */
+};
+
+/* per-candidate flag bits */
+enum {
+    ATP_FLAG_FEASIBLE = 1,    /* min U_ESM over the trajectory > 0 and finite (Sec. IV-B) */
+    ATP_FLAG_DONE = 2,        /* reached the goal circle and was frozen (Sec. IV-C) */
+    ATP_FLAG_OFFMAP = 4,      /* a wheel queried the terrain outside the map */
+    ATP_FLAG_NONFINITE = 8    /* state or cost became NaN/inf */
+};
+
+/* Vehicle parameters in SI units (App. A notation, App. B values).
+ * L_f, L_r: CoM to front / rear axle; e: track; hR: h + R, the CoM height
+ * above the contact patches; k, b: spring and damper rate of each front /
+ * rear corner; C, mu: sigmoid tire model (Sec. III-A); delta_max: steering
+ * angle limit; delta_rate_max: steering rate limit (Sec. IV-C); g: gravity. */
+typedef struct {
+    double M, Jxx, Jyy, Jzz;
+    double Lf, Lr, e, hR;
+    double kf, kr, bf, br;
+    double C, mu;
+    double delta_max, delta_rate_max, g;
+} atp_vehicle;
+
+/* Cost of Sec. IV-C: L = w_t + w_c delta_dot^2 + sigma max(0, 1 - U/eps)^2
+ * + sum over wheels of the costmap, Phi = w_g |p_xy - goal|; the horizon is
+ * truncated when |p_xy - goal| <= goal_r.  eps_esm <= 0 selects 10 % of the
+ * level-ground ESM.  All weights must be >= 0. */
+typedef struct {
+    double wt, wc, wg, sigma, eps_esm, goal_x, goal_y, goal_r;
+} atp_cost;
+
+/* one SRB state, the 13 floats in the order given above */
+typedef struct {
+    float x, y, z, psi, theta, phi, vx, vy, vz, wx, wy, wz, delta;
+} atp_state;
+
+/* A prepared terrain (see atp_terrain_prepare).  texels is a device pointer
+ * owned by the caller, nx * ny texels of the given format. */
+typedef struct {
+    const void *texels;
+    int nx, ny;
+    double cell, x0, y0;      /* node (i, j) is at (x0 + i cell, y0 + j cell) */
+    int format;
+} atp_terrain;
+
+/* Result of a plan, written to device memory. */
+typedef struct {
+    uint32_t best_idx;        /* index of the best candidate (Sec. IV-D, reading Q7) */
+    uint32_t n_feasible;      /* number of feasible candidates */
+    float best_cost;          /* J of the best candidate */
+    float best_min_margin;    /* its minimum U_ESM over the trajectory [J] */
+    int32_t best_min_step;    /* control step holding that minimum */
+    uint32_t reserved;
+} atp_plan_out;
+
+/* --------------------------------------------------------------------- */
+int atp_version(void);
+
+/* Create a context on `device` (made current for the call).  Allocates the
+ * small reduction scratch.  Returns ATP_ERR_CUDA / ATP_ERR_NOMEM on failure,
+ * with *ctx set to NULL. */
+struct atp_ctx;
+typedef struct atp_ctx atp_ctx;
+int atp_create(atp_ctx **ctx, int device);
+
+/* Free the context and its scratch.  Waits for the device first. */
+int atp_destroy(atp_ctx *ctx);
+
+/* One-line description of the last error on this context ("" if none). */
+const char *atp_last_error(const atp_ctx *ctx);
+
+/* Pre-size the context scratch for plans of up to N candidates and H control
+ * steps, so that later calls allocate nothing.  Without it, atp_plan grows the
+ * scratch on first use of a larger size (a synchronous cudaMalloc). */
+int atp_reserve(atp_ctx *ctx, int N, int H);
+
+/* Bytes of device memory a prepared terrain of nx x ny nodes needs. */
+size_t atp_terrain_bytes(int nx, int ny, int format);
+
+/* Build the texels of a terrain: per node the height, its slope f_x, f_y by
+ * central differences (one-sided on the border) and the optional costmap
+ * value, the numeric-slope heightmap of Sec. III-A and the interpolated
+ * costmap of Sec. IV-D (reading Q10).
+ *   heights_dev  float [ny][nx], device
+ *   costmap_dev  float [ny][nx] summed soft-constraint cost rate, or NULL (0)
+ *   texels_dev   atp_terrain_bytes(nx, ny, format) bytes, 16-byte aligned
+ * nx, ny >= 3, cell > 0.  Fills *out (may be NULL) with the terrain handle. */
+int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *costmap_dev,
+                        int nx, int ny, double cell, double x0, double y0, int format,
+                        void *texels_dev, atp_terrain *out, void *stream);
+
+/* Plan: roll out N candidates over H control steps and reduce to the best.
+ *
+ *   x0            host state shared by every candidate, or NULL when
+ *   x0_dev        float [13][N] device SoA of per-candidate initial states
+ *                 (row q holds state component q of every candidate)
+ *   ctrl_dev      float2 ctrl[H][N] device, 8-byte aligned
+ *   dt, n_sub     zero-order-hold interval and Euler steps per interval
+ *   out_dev       atp_plan_out, device
+ *   best_ctrl_dev float [H][2] or NULL: the best candidate's controls with the
+ *                 steering rate clamped as used
+ *   best_margin_dev float [H] or NULL: the best candidate's minimum U_ESM over
+ *                 each control step (the final state folded into step H-1)
+ *   cand_cost_dev, cand_margin_dev  float [N] or NULL: J and min U_ESM
+ *   cand_flags_dev uint8 [N] or NULL: ATP_FLAG_* bits
+ *   cand_xf_dev   float [13][N] or NULL: final states, SoA
+ *   stream        cudaStream_t
+ * 1 <= N <= 2^31 - 1, H >= 1, dt > 0, 0 <= n_sub.  Validation failures return
+ * ATP_ERR_INVALID; launch failures ATP_ERR_CUDA. */
+int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+             const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
+             const float *ctrl_dev, int N, int H, float dt, int n_sub,
+             atp_plan_out *out_dev, float *best_ctrl_dev, float *best_margin_dev,
+             float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
+             float *cand_xf_dev, void *stream);
+
+/* Batched rollout without the reduction: the same per-candidate results as
+ * atp_plan (cost, margin, flags, final states, per-step margins
+ * step_margin_dev float [H][N] or NULL), nothing else. */
+int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
+                const float *ctrl_dev, int N, int H, float dt, int n_sub,
+                float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
+                float *cand_xf_dev, float *step_margin_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATP_H */

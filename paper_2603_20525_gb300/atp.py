@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libatp.so (include/atp.h).
+
+Argument marshalling only: device memory comes from PyTorch tensors, whose
+raw pointers and the current CUDA stream handle are passed to the C-ABI.
+Every step of the planner runs in the library's CUDA kernels; if the library
+cannot be loaded the binding raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+ATP_OK = 0
+ERRORS = {-1: "ATP_ERR_INVALID", -2: "ATP_ERR_UNSUPPORTED", -3: "ATP_ERR_NOMEM",
+          -4: "ATP_ERR_CUDA", -5: "ATP_ERR_TIMEOUT"}
+F32X4, BF16X4 = 0, 1
+FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
+
+# every symbol include/atp.h declares
+EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
+           "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout")
+
+
+class Vehicle(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("M", "Jxx", "Jyy", "Jzz", "Lf", "Lr", "e", "hR",
+                                          "kf", "kr", "bf", "br", "C", "mu", "delta_max",
+                                          "delta_rate_max", "g")]
+
+
+class Cost(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("wt", "wc", "wg", "sigma", "eps_esm",
+                                          "goal_x", "goal_y", "goal_r")]
+
+
+class State(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("x", "y", "z", "psi", "theta", "phi", "vx", "vy",
+                                         "vz", "wx", "wy", "wz", "delta")]
+
+
+class TerrainC(C.Structure):
+    _fields_ = [("texels", C.c_void_p), ("nx", C.c_int), ("ny", C.c_int),
+                ("cell", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
+                ("format", C.c_int)]
+
+
+class PlanOut(C.Structure):
+    _fields_ = [("best_idx", C.c_uint32), ("n_feasible", C.c_uint32),
+                ("best_cost", C.c_float), ("best_min_margin", C.c_float),
+                ("best_min_step", C.c_int32), ("reserved", C.c_uint32)]
+
+
+_vp = C.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libatp.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libatp.so not found at {path}; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        L.atp_version.restype = C.c_int
+        L.atp_create.argtypes = [C.POINTER(_vp), C.c_int]
+        L.atp_destroy.argtypes = [_vp]
+        L.atp_last_error.argtypes = [_vp]
+        L.atp_last_error.restype = C.c_char_p
+        L.atp_reserve.argtypes = [_vp, C.c_int, C.c_int]
+        L.atp_terrain_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.atp_terrain_bytes.restype = C.c_size_t
+        L.atp_terrain_prepare.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double,
+                                          C.c_double, C.c_int, _vp, C.POINTER(TerrainC), _vp]
+        L.atp_plan.argtypes = [_vp, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
+                               C.POINTER(State), _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
+                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.atp_rollout.argtypes = [_vp, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
+                                  C.POINTER(State), _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
+                                  _vp, _vp, _vp, _vp, _vp, _vp]
+        for n in ("atp_create", "atp_destroy", "atp_reserve", "atp_terrain_prepare",
+                  "atp_plan", "atp_rollout"):
+            getattr(L, n).restype = C.c_int
+        _lib = L
+        return L
+
+
+def vehicle(d: dict) -> Vehicle:
+    return Vehicle(**{k: float(d[k]) for k, _ in Vehicle._fields_})
+
+
+def cost(d: dict) -> Cost:
+    return Cost(**{k: float(d[k]) for k, _ in Cost._fields_})
+
+
+def state(x) -> State:
+    return State(*[float(v) for v in x])
+
+
+class AtpError(RuntimeError):
+    pass
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Terrain:
+    """A prepared terrain: the texel tensor (kept alive here) and its handle."""
+
+    def __init__(self, texels, handle: TerrainC):
+        self.texels = texels
+        self.c = handle
+
+
+class Context:
+    """One atp_ctx on one device (not thread-safe; one per stream)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.h = C.c_void_p()
+        rc = self.lib.atp_create(C.byref(self.h), int(device))
+        if rc != ATP_OK:
+            raise AtpError(f"atp_create failed: {ERRORS.get(rc, rc)}")
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.atp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != ATP_OK:
+            msg = self.lib.atp_last_error(self.h).decode()
+            raise AtpError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
+
+    def reserve(self, N: int, H: int):
+        self._check(self.lib.atp_reserve(self.h, int(N), int(H)), "atp_reserve")
+
+    def terrain_prepare(self, heights, cell, x0=0.0, y0=0.0, costmap=None, fmt=F32X4, stream=None):
+        """heights: float32 CUDA tensor [ny, nx]; returns a Terrain."""
+        import torch
+        ny, nx = heights.shape
+        nbytes = self.lib.atp_terrain_bytes(nx, ny, fmt)
+        tex = torch.empty(nbytes // 4, dtype=torch.float32, device=heights.device)
+        h = TerrainC()
+        rc = self.lib.atp_terrain_prepare(self.h, _ptr(heights), _ptr(costmap), nx, ny,
+                                          float(cell), float(x0), float(y0), int(fmt),
+                                          _ptr(tex), C.byref(h), _stream(stream))
+        self._check(rc, "atp_terrain_prepare")
+        return Terrain(tex, h)
+
+    def plan(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0, out=None,
+             stream=None, want_candidates=True, want_xf=False):
+        """Plan over ctrl (float32 CUDA [H, N, 2]).  x0: 13 floats (host) or a
+        float32 CUDA tensor [13, N] of per-candidate states.  Returns a dict of
+        CUDA tensors; nothing is synchronized."""
+        import torch
+        H, N, _ = ctrl.shape
+        dev = ctrl.device
+        o = out if out is not None else {}
+        if "out" not in o:
+            o["out"] = torch.zeros(6, dtype=torch.int32, device=dev)
+            o["best_ctrl"] = torch.empty((H, 2), dtype=torch.float32, device=dev)
+            o["best_margin"] = torch.empty(H, dtype=torch.float32, device=dev)
+            if want_candidates:
+                o["cost"] = torch.empty(N, dtype=torch.float32, device=dev)
+                o["margin"] = torch.empty(N, dtype=torch.float32, device=dev)
+                o["flags"] = torch.empty(N, dtype=torch.uint8, device=dev)
+            if want_xf:
+                o["xf"] = torch.empty((13, N), dtype=torch.float32, device=dev)
+        xs, xdev = (None, x0) if isinstance(x0, torch.Tensor) else (state(x0), None)
+        rc = self.lib.atp_plan(self.h, C.byref(vehicle(veh)), C.byref(cost(cst)),
+                               C.byref(terrain.c), C.byref(xs) if xs is not None else None,
+                               _ptr(xdev), _ptr(ctrl), int(N), int(H), float(dt), int(n_sub),
+                               _ptr(o["out"]), _ptr(o.get("best_ctrl")), _ptr(o.get("best_margin")),
+                               _ptr(o.get("cost")), _ptr(o.get("margin")), _ptr(o.get("flags")),
+                               _ptr(o.get("xf")), _stream(stream))
+        self._check(rc, "atp_plan")
+        return o
+
+    def rollout(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0,
+                want_xf=True, want_step_margin=False, stream=None):
+        import torch
+        H, N, _ = ctrl.shape
+        dev = ctrl.device
+        o = dict(cost=torch.empty(N, dtype=torch.float32, device=dev),
+                 margin=torch.empty(N, dtype=torch.float32, device=dev),
+                 flags=torch.empty(N, dtype=torch.uint8, device=dev))
+        if want_xf:
+            o["xf"] = torch.empty((13, N), dtype=torch.float32, device=dev)
+        if want_step_margin:
+            o["step_margin"] = torch.empty((H, N), dtype=torch.float32, device=dev)
+        xs, xdev = (None, x0) if isinstance(x0, torch.Tensor) else (state(x0), None)
+        rc = self.lib.atp_rollout(self.h, C.byref(vehicle(veh)), C.byref(cost(cst)),
+                                  C.byref(terrain.c), C.byref(xs) if xs is not None else None,
+                                  _ptr(xdev), _ptr(ctrl), int(N), int(H), float(dt), int(n_sub),
+                                  _ptr(o["cost"]), _ptr(o["margin"]), _ptr(o["flags"]),
+                                  _ptr(o.get("xf")), _ptr(o.get("step_margin")), _stream(stream))
+        self._check(rc, "atp_rollout")
+        return o
+
+
+def decode_out(t) -> dict:
+    """The 24-byte atp_plan_out tensor (int32 [6]) as a dict (host copy)."""
+    import numpy as np
+    a = t.detach().cpu().numpy().astype(np.int32)
+    return dict(best_idx=int(np.uint32(a[0])), n_feasible=int(np.uint32(a[1])),
+                best_cost=float(a[2:3].view(np.float32)[0]),
+                best_min_margin=float(a[3:4].view(np.float32)[0]),
+                best_min_step=int(a[4]))

@@ -1,0 +1,406 @@
+// api.cu - the C-ABI of include/atp.h: argument validation, the context and
+// its scratch, FP64 -> FP32 parameter derivation and kernel launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "atp.h"
+#include "plan_kernel.cuh"
+
+struct atp_ctx {
+    int device;
+    char err[256];
+    void *scratch;            // atp::Scratch + per-candidate buffers
+    size_t scratch_bytes;
+    int capN, capH;
+};
+
+namespace {
+
+int fail(atp_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(atp_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, e == cudaErrorMemoryAllocation ? ATP_ERR_NOMEM : ATP_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// Selects ctx->device for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+        else if (err == cudaSuccess) prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool fin(double v) { return std::isfinite(v); }
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct ScratchLayout {
+    size_t cost, margin, flags, step_margin, total;
+};
+
+ScratchLayout layout(size_t N, size_t H)
+{
+    ScratchLayout L;
+    size_t o = align_up(sizeof(atp::Scratch));
+    L.cost = o;        o = align_up(o + N * sizeof(float));
+    L.margin = o;      o = align_up(o + N * sizeof(float));
+    L.flags = o;       o = align_up(o + N);
+    L.step_margin = o; o = align_up(o + N * H * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+int ensure_scratch(atp_ctx *ctx, int N, int H)
+{
+    if (ctx->scratch && N <= ctx->capN && H <= ctx->capH) return ATP_OK;
+    const int nN = N > ctx->capN ? N : ctx->capN;
+    const int nH = H > ctx->capH ? H : ctx->capH;
+    const ScratchLayout L = layout((size_t)nN, (size_t)nH);
+    if (ctx->scratch) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize before growing scratch");
+        cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->capN = ctx->capH = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
+    atp::Scratch init{~0ull, 0u, 0u};
+    e = cudaMemcpy(p, &init, sizeof init, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return cuda_fail(ctx, e, "scratch initialisation");
+    }
+    ctx->scratch = p;
+    ctx->scratch_bytes = L.total;
+    ctx->capN = nN;
+    ctx->capH = nH;
+    return ATP_OK;
+}
+
+int check_vehicle(atp_ctx *ctx, const atp_vehicle *v)
+{
+    if (!v) return fail(ctx, ATP_ERR_INVALID, "vehicle is NULL");
+    const double a[] = {v->M, v->Jxx, v->Jyy, v->Jzz, v->Lf, v->Lr, v->e, v->hR, v->kf, v->kr,
+                        v->bf, v->br, v->C, v->mu, v->delta_max, v->delta_rate_max, v->g};
+    for (double x : a)
+        if (!fin(x)) return fail(ctx, ATP_ERR_INVALID, "vehicle parameter is not finite");
+    if (!(v->M > 0 && v->Jxx > 0 && v->Jyy > 0 && v->Jzz > 0))
+        return fail(ctx, ATP_ERR_INVALID, "mass and inertias must be > 0");
+    if (!(v->Lf > 0 && v->Lr > 0 && v->e > 0 && v->hR > 0))
+        return fail(ctx, ATP_ERR_INVALID, "Lf, Lr, e, h+R must be > 0");
+    if (!(v->kf >= 0 && v->kr >= 0 && v->bf >= 0 && v->br >= 0 && v->C >= 0 && v->mu > 0 &&
+          v->delta_max >= 0 && v->delta_rate_max >= 0 && v->g >= 0))
+        return fail(ctx, ATP_ERR_INVALID, "k, b, C, delta limits, g must be >= 0 and mu > 0");
+    return ATP_OK;
+}
+
+int check_cost(atp_ctx *ctx, const atp_cost *c)
+{
+    if (!c) return fail(ctx, ATP_ERR_INVALID, "cost is NULL");
+    const double a[] = {c->wt, c->wc, c->wg, c->sigma, c->eps_esm, c->goal_x, c->goal_y, c->goal_r};
+    for (double x : a)
+        if (!fin(x)) return fail(ctx, ATP_ERR_INVALID, "cost parameter is not finite");
+    if (!(c->wt >= 0 && c->wc >= 0 && c->wg >= 0 && c->sigma >= 0 && c->goal_r >= 0))
+        return fail(ctx, ATP_ERR_INVALID, "cost weights and goal radius must be >= 0");
+    return ATP_OK;
+}
+
+int check_terrain(atp_ctx *ctx, const atp_terrain *t)
+{
+    if (!t || !t->texels) return fail(ctx, ATP_ERR_INVALID, "terrain or its texels is NULL");
+    if (t->format != ATP_TERRAIN_F32X4)
+        return fail(ctx, ATP_ERR_UNSUPPORTED, "terrain format %d not supported by this call", t->format);
+    if (t->nx < 3 || t->ny < 3 || t->nx > 65536 || t->ny > 65536)
+        return fail(ctx, ATP_ERR_INVALID, "terrain must be between 3 and 65536 nodes per side");
+    if (!(t->cell > 0.0) || !std::isfinite(t->cell) || !std::isfinite(t->x0) || !std::isfinite(t->y0))
+        return fail(ctx, ATP_ERR_INVALID, "terrain cell must be > 0 and origin finite");
+    if ((uintptr_t)t->texels % 16 != 0) return fail(ctx, ATP_ERR_INVALID, "texels must be 16-byte aligned");
+    return ATP_OK;
+}
+
+// v = hi + lo with hi = fl(v), lo = fl(v - hi)
+void split(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// FP64 derivation of the kernel constants (Sec. III-A load transfer, Sec.
+// IV-A preload, Sec. IV-B ESM geometry, Sec. IV-C cost).
+void derive(const atp_vehicle &v, const atp_cost &c, const atp_terrain &t, atp::PlanParams &p)
+{
+    const double L = v.Lf + v.Lr;
+    const double Kzzf = v.M * v.Lr / L, Kzzr = v.M * v.Lf / L;
+    const double Rbar = std::sqrt(v.hR * v.hR + 0.25 * v.e * v.e);
+    const double phibar = std::atan(2.0 * v.hR / v.e);
+    atp::Veh &V = p.V;
+    V.M = (float)v.M;
+    V.halfM = (float)(0.5 * v.M);
+    V.invM = (float)(1.0 / v.M);
+    V.dJyz = (float)(v.Jyy - v.Jzz);
+    V.dJxz = (float)(v.Jxx - v.Jzz);
+    V.dJxy = (float)(v.Jxx - v.Jyy);
+    V.invJxx = (float)(1.0 / v.Jxx);
+    V.invJyy = (float)(1.0 / v.Jyy);
+    V.invJzz = (float)(1.0 / v.Jzz);
+    V.Lf = (float)v.Lf;
+    V.Lr = (float)v.Lr;
+    V.he = (float)(0.5 * v.e);
+    V.hR = (float)v.hR;
+    V.kf = (float)v.kf;
+    V.kr = (float)v.kr;
+    V.bf = (float)v.bf;
+    V.br = (float)v.br;
+    V.Fsf = (float)(0.5 * v.g * Kzzf);
+    V.Fsr = (float)(0.5 * v.g * Kzzr);
+    V.C = (float)v.C;
+    V.mu = (float)v.mu;
+    V.mu2 = (float)(v.mu * v.mu);
+    V.dmax = (float)v.delta_max;
+    V.ddmax = (float)v.delta_rate_max;
+    V.g = (float)v.g;
+    V.MgRbar = (float)(v.M * v.g * Rbar);
+    V.cpb = (float)std::cos(phibar);
+    V.spb = (float)std::sin(phibar);
+    V.tip = (float)(0.5 * M_PI - phibar);
+    const double U0 = v.M * v.g * Rbar * (1.0 - std::sin(phibar));
+    const double eps = c.eps_esm > 0 ? c.eps_esm : 0.1 * U0;
+    atp::Cost &C = p.C;
+    C.wt = (float)c.wt;
+    C.wc = (float)c.wc;
+    C.wg = (float)c.wg;
+    C.sigma = (float)c.sigma;
+    C.inv_eps = (float)(1.0 / eps);
+    split(c.goal_x - t.x0, C.gx_hi, C.gx_lo);
+    split(c.goal_y - t.y0, C.gy_hi, C.gy_lo);
+    C.goal_r2 = (float)(c.goal_r * c.goal_r);
+    atp::Terrain &T = p.T;
+    T.tex = (const float4 *)t.texels;
+    T.nx = t.nx;
+    T.ny = t.ny;
+    T.inv_cell = (float)(1.0 / t.cell);
+    split(t.x0, T.x0_hi, T.x0_lo);
+    split(t.y0, T.y0_hi, T.y0_lo);
+}
+
+int common_checks(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *ter,
+                  const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int N, int H,
+                  float dt, int n_sub, int *n_sub_out)
+{
+    int rc;
+    if ((rc = check_vehicle(ctx, veh)) != ATP_OK) return rc;
+    if ((rc = check_cost(ctx, cost)) != ATP_OK) return rc;
+    if ((rc = check_terrain(ctx, ter)) != ATP_OK) return rc;
+    if (!x0 && !x0_dev) return fail(ctx, ATP_ERR_INVALID, "need x0 or x0_dev");
+    if (x0) {
+        const float *s = &x0->x;
+        for (int q = 0; q < 13; ++q)
+            if (!std::isfinite(s[q])) return fail(ctx, ATP_ERR_INVALID, "x0 is not finite");
+    }
+    if (!ctrl_dev) return fail(ctx, ATP_ERR_INVALID, "ctrl_dev is NULL");
+    if ((uintptr_t)ctrl_dev % 8 != 0) return fail(ctx, ATP_ERR_INVALID, "ctrl_dev must be 8-byte aligned");
+    if (N < 1) return fail(ctx, ATP_ERR_INVALID, "N must be >= 1");
+    if (H < 1) return fail(ctx, ATP_ERR_INVALID, "H must be >= 1");
+    if (!(dt > 0.f) || !std::isfinite(dt)) return fail(ctx, ATP_ERR_INVALID, "dt must be finite and > 0");
+    if (n_sub < 0 || n_sub > 1000000) return fail(ctx, ATP_ERR_INVALID, "n_sub must be in [0, 1e6]");
+    if (n_sub == 0) {
+        double q = std::ceil((double)dt / 0.005 - 1e-9);
+        n_sub = q < 1.0 ? 1 : (int)q;
+    }
+    *n_sub_out = n_sub;
+    return ATP_OK;
+}
+
+void fill_problem(atp::PlanParams &p, const atp_state *x0, const float *x0_dev, const float *ctrl,
+                  int N, int H, float dt, int n_sub)
+{
+    if (x0) {
+        std::memcpy(p.x0, &x0->x, sizeof p.x0);
+        p.x0_soa = nullptr;
+    } else {
+        std::memset(p.x0, 0, sizeof p.x0);
+        p.x0_soa = x0_dev;
+    }
+    p.ctrl = (const float2 *)ctrl;
+    p.N = N;
+    p.H = H;
+    p.n_sub = n_sub;
+    p.h = (float)((double)dt / (double)n_sub);
+}
+
+}  // namespace
+
+extern "C" {
+
+int atp_version(void) { return ATP_VERSION; }
+
+int atp_create(atp_ctx **out, int device)
+{
+    if (!out) return ATP_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return ATP_ERR_INVALID;
+    atp_ctx *ctx = new (std::nothrow) atp_ctx();
+    if (!ctx) return ATP_ERR_NOMEM;
+    ctx->device = device;
+    ctx->err[0] = 0;
+    DeviceGuard g(device);
+    if (g.err != cudaSuccess) {
+        delete ctx;
+        return ATP_ERR_CUDA;
+    }
+    int rc = ensure_scratch(ctx, 1, 1);
+    if (rc != ATP_OK) {
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return ATP_OK;
+}
+
+int atp_destroy(atp_ctx *ctx)
+{
+    if (!ctx) return ATP_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    delete ctx;
+    return ATP_OK;
+}
+
+const char *atp_last_error(const atp_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+int atp_reserve(atp_ctx *ctx, int N, int H)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (N < 1 || H < 1) return fail(ctx, ATP_ERR_INVALID, "reserve needs N, H >= 1");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    return ensure_scratch(ctx, N, H);
+}
+
+size_t atp_terrain_bytes(int nx, int ny, int format)
+{
+    if (nx < 1 || ny < 1) return 0;
+    const size_t per = format == ATP_TERRAIN_BF16X4 ? 8 : 16;
+    return (size_t)nx * (size_t)ny * per;
+}
+
+int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *costmap_dev, int nx,
+                        int ny, double cell, double x0, double y0, int format, void *texels_dev,
+                        atp_terrain *out, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (!heights_dev || !texels_dev) return fail(ctx, ATP_ERR_INVALID, "heights or texels is NULL");
+    if (nx < 3 || ny < 3 || nx > 65536 || ny > 65536)
+        return fail(ctx, ATP_ERR_INVALID, "terrain must be between 3 and 65536 nodes per side");
+    if (!(cell > 0.0) || !std::isfinite(cell) || !std::isfinite(x0) || !std::isfinite(y0))
+        return fail(ctx, ATP_ERR_INVALID, "cell must be > 0 and origin finite");
+    if (format != ATP_TERRAIN_F32X4)
+        return fail(ctx, ATP_ERR_UNSUPPORTED, "terrain format %d not supported", format);
+    if ((uintptr_t)texels_dev % 16 != 0) return fail(ctx, ATP_ERR_INVALID, "texels must be 16-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    cudaError_t e = atp::launch_terrain_prepare_f32(heights_dev, costmap_dev, nx, ny,
+                                                    (float)(1.0 / cell), (float4 *)texels_dev,
+                                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "terrain prepare launch");
+    if (out) {
+        out->texels = texels_dev;
+        out->nx = nx;
+        out->ny = ny;
+        out->cell = cell;
+        out->x0 = x0;
+        out->y0 = y0;
+        out->format = format;
+    }
+    return ATP_OK;
+}
+
+int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
+             const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int N, int H, float dt,
+             int n_sub, atp_plan_out *out_dev, float *best_ctrl_dev, float *best_margin_dev,
+             float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
+             float *cand_xf_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int ns = 0;
+    int rc = common_checks(ctx, veh, cost, terrain, x0, x0_dev, ctrl_dev, N, H, dt, n_sub, &ns);
+    if (rc != ATP_OK) return rc;
+    if (!out_dev) return fail(ctx, ATP_ERR_INVALID, "out_dev is NULL");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    if ((rc = ensure_scratch(ctx, N, H)) != ATP_OK) return rc;
+    const ScratchLayout L = layout((size_t)ctx->capN, (size_t)ctx->capH);
+    char *base = (char *)ctx->scratch;
+    atp::PlanParams p;
+    std::memset(&p, 0, sizeof p);
+    derive(*veh, *cost, *terrain, p);
+    fill_problem(p, x0, x0_dev, ctrl_dev, N, H, dt, ns);
+    p.cost = cand_cost_dev ? cand_cost_dev : (float *)(base + L.cost);
+    p.margin = cand_margin_dev ? cand_margin_dev : (float *)(base + L.margin);
+    p.flags = cand_flags_dev ? cand_flags_dev : (uint8_t *)(base + L.flags);
+    p.xf = cand_xf_dev;
+    p.step_margin = (float *)(base + L.step_margin);
+    p.out = out_dev;
+    p.best_ctrl = best_ctrl_dev;
+    p.best_margin = best_margin_dev;
+    p.scratch = (atp::Scratch *)base;
+    cudaError_t e = atp::launch_plan(p, true, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
+    return ATP_OK;
+}
+
+int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
+                const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int N, int H,
+                float dt, int n_sub, float *cand_cost_dev, float *cand_margin_dev,
+                uint8_t *cand_flags_dev, float *cand_xf_dev, float *step_margin_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int ns = 0;
+    int rc = common_checks(ctx, veh, cost, terrain, x0, x0_dev, ctrl_dev, N, H, dt, n_sub, &ns);
+    if (rc != ATP_OK) return rc;
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    atp::PlanParams p;
+    std::memset(&p, 0, sizeof p);
+    derive(*veh, *cost, *terrain, p);
+    fill_problem(p, x0, x0_dev, ctrl_dev, N, H, dt, ns);
+    p.cost = cand_cost_dev;
+    p.margin = cand_margin_dev;
+    p.flags = cand_flags_dev;
+    p.xf = cand_xf_dev;
+    p.step_margin = step_margin_dev;
+    cudaError_t e = atp::launch_plan(p, false, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
+    return ATP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,333 @@
+// plan_kernel.cu - fused SRB rollout, cost, ESM margin and empirical argmin
+// (arxiv 2603.20525, Sec. IV-A..IV-D) for sm_103a.
+//
+// Design
+//   * One thread per candidate.  Its state stays in registers for the whole
+//     horizon; per Euler step the only memory traffic is 16 terrain texels
+//     (four bilinear lookups of one float4 per corner) through the read-only
+//     path, which the L1 and the 126 MB L2 serve for every terrain size used.
+//   * Controls are time-major float2 [H][N]: a warp reads one coalesced 256 B
+//     line per control step.
+//   * The reduction is fused into the tail: a warp-shuffle min of a packed
+//     64-bit key (infeasible bit, order-preserving image of the FP32 cost,
+//     candidate index), one shared-memory step per CTA, one 64-bit atomicMin
+//     per CTA, a ballot/popc feasible count, and a ticket that elects the last
+//     CTA to write the result and the best candidate's controls and margins.
+#include "plan_kernel.cuh"
+
+#include <math_constants.h>
+
+namespace atp {
+
+__device__ __forceinline__ uint32_t order_u32(float f)
+{
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float clamp_keep_nan(float v, float lo, float hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+template <bool PER_X0, bool REDUCE>
+__global__ void __launch_bounds__(kPlanBlock)
+plan_kernel(const __grid_constant__ PlanParams p)
+{
+    const Veh &V = p.V;
+    const Cost &Cc = p.C;
+    const Terrain &T = p.T;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = j < p.N;
+
+    float J = 0.f, margin = CUDART_INF_F;
+    bool feasible = false;
+
+    if (live) {
+        // state; x, y relative to the terrain origin; *_l are the low parts of
+        // the compensated components
+        float x, xl, y, yl, z, zl, psi, psil, vx, vxl, vy, vyl, vz, vzl;
+        float th, ph, wx, wy, wz, d;
+        {
+            float q[13];
+            if (PER_X0) {
+                const size_t N = (size_t)p.N;
+#pragma unroll
+                for (int c = 0; c < 13; ++c) q[c] = p.x0_soa[c * N + j];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 13; ++c) q[c] = p.x0[c];
+            }
+            two_sum(q[0], -T.x0_hi, x, xl);
+            xl -= T.x0_lo;
+            two_sum(q[1], -T.y0_hi, y, yl);
+            yl -= T.y0_lo;
+            z = q[2]; psi = q[3]; th = q[4]; ph = q[5];
+            vx = q[6]; vy = q[7]; vz = q[8];
+            wx = q[9]; wy = q[10]; wz = q[11]; d = q[12];
+            zl = psil = vxl = vyl = vzl = 0.f;
+        }
+        bool done = false, off = false;
+        const float h = p.h;
+        float Ufrozen = 0.f;
+
+        for (int k = 0; k < p.H; ++k) {
+            // zero-order hold; admissible steering rate |delta_dot| <= max
+            const float2 u = __ldg(p.ctrl + (size_t)k * p.N + j);
+            const float dd = clamp_keep_nan(u.x, -V.ddmax, V.ddmax);
+            const float ax = u.y;
+            float sm = CUDART_INF_F;
+            for (int q = 0; q < p.n_sub; ++q) {
+                if (done) {            // frozen at the goal: the same state each step
+                    sm = fminf(sm, Ufrozen);
+                    continue;
+                }
+                float sps, cps, sth, cth, sph, cph;
+                sincosf(psi, &sps, &cps);
+                sincosf(th, &sth, &cth);
+                sincosf(ph, &sph, &cph);
+                const float U = esm(V, ph, sph, cph, cth);
+                margin = fminf(margin, U);
+                sm = fminf(sm, U);
+                // goal test before the step (Sec. IV-C, reading Q4)
+                const float gdx = (x - Cc.gx_hi) + (xl - Cc.gx_lo);
+                const float gdy = (y - Cc.gy_hi) + (yl - Cc.gy_lo);
+                if (fmaf(gdx, gdx, gdy * gdy) <= Cc.goal_r2) {
+                    done = true;
+                    Ufrozen = U;
+                    continue;
+                }
+                // 3-2-1 rotation, body -> world (Sec. IV-A)
+                Body B;
+                float *R = B.R;
+                R[0] = cps * cth;
+                R[1] = cps * sph * sth - cph * sps;
+                R[2] = sph * sps + cph * cps * sth;
+                R[3] = cth * sps;
+                R[4] = cph * cps + sph * sps * sth;
+                R[5] = cph * sps * sth - cps * sph;
+                R[6] = -sth;
+                R[7] = cth * sph;
+                R[8] = cph * cth;
+                cell_split(x, xl, T.inv_cell, B.icx, B.fcx);
+                cell_split(y, yl, T.inv_cell, B.icy, B.fcy);
+                B.z_hi = z;
+                B.z_lo = zl;
+                B.vx = vx; B.vy = vy; B.vz = vz;
+                B.wx = wx; B.wy = wy; B.wz = wz;
+                // gravity in B: R^T (0, 0, -g)
+                const float gBx = -V.g * R[6], gBy = -V.g * R[7], gBz = -V.g * R[8];
+                const WheelOut fl = wheel(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, off);
+                const WheelOut fr = wheel(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, off);
+                const WheelOut rl = wheel(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                const WheelOut rr = wheel(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                // summed forces and moments; rear longitudinal constraint force
+                const float cd = cosf(d);
+                const float Fyf = (fl.Fy + fr.Fy) * cd;
+                const float Fyr = rl.Fy + rr.Fy;
+                const float FyB = Fyf + Fyr;
+                const float FzB = (fl.Fz + fr.Fz) + (rl.Fz + rr.Fz);
+                const float Fx = V.halfM * (ax - gBx + wy * vz - wz * vy);
+                const float Mx = V.he * ((fl.Fz - fr.Fz) + (rl.Fz - rr.Fz)) + V.hR * FyB;
+                const float My = -V.hR * (2.f * Fx) - V.Lf * (fl.Fz + fr.Fz) + V.Lr * (rl.Fz + rr.Fz);
+                const float Mz = V.Lf * Fyf - V.Lr * Fyr;
+                // running cost L = L_0 + L_soft (Sec. IV-C), left Riemann sum
+                const float soft = fmaxf(1.f - U * Cc.inv_eps, 0.f);
+                const float L = Cc.wt + Cc.wc * dd * dd + Cc.sigma * soft * soft +
+                                ((fl.cost + fr.cost) + (rl.cost + rr.cost));
+                J = fmaf(h, L, J);
+                // state derivative A(xi) + B zeta (Sec. IV-A)
+                const float ic = 1.f / cth;
+                const float wsc = sph * wy + cph * wz;
+                const float dx = R[0] * vx + R[1] * vy + R[2] * vz;
+                const float dy = R[3] * vx + R[4] * vy + R[5] * vz;
+                const float dz = R[6] * vx + R[7] * vy + R[8] * vz;
+                const float dpsi = wsc * ic;
+                const float dth = cph * wy - sph * wz;
+                const float dph = wx + wsc * (sth * ic);
+                const float dvy = FyB * V.invM + gBy + wx * vz - wz * vx;
+                const float dvz = FzB * V.invM + gBz - wx * vy + wy * vx;
+                const float dwx = (Mx + V.dJyz * wy * wz) * V.invJxx;
+                const float dwy = (My - V.dJxz * wx * wz) * V.invJyy;
+                const float dwz = (Mz + V.dJxy * wx * wy) * V.invJzz;
+                // forward Euler (Sec. IV-D), steering angle clamped (reading Q5)
+                acc2(x, xl, h * dx);
+                acc2(y, yl, h * dy);
+                acc2(z, zl, h * dz);
+                acc2(psi, psil, h * dpsi);
+                th = fmaf(h, dth, th);
+                ph = fmaf(h, dph, ph);
+                acc2(vx, vxl, h * ax);
+                acc2(vy, vyl, h * dvy);
+                acc2(vz, vzl, h * dvz);
+                wx = fmaf(h, dwx, wx);
+                wy = fmaf(h, dwy, wy);
+                wz = fmaf(h, dwz, wz);
+                d = clamp_keep_nan(fmaf(h, dd, d), -V.dmax, V.dmax);
+            }
+            if (p.step_margin) p.step_margin[(size_t)k * p.N + j] = sm;
+        }
+        // final state: margin, goal test, terminal cost Phi (Sec. IV-C)
+        {
+            float sth, cth, sph, cph;
+            sincosf(th, &sth, &cth);
+            sincosf(ph, &sph, &cph);
+            const float U = esm(V, ph, sph, cph, cth);
+            margin = fminf(margin, U);
+            if (p.step_margin) {
+                float *e = p.step_margin + (size_t)(p.H - 1) * p.N + j;
+                *e = fminf(*e, U);
+            }
+            const float gdx = (x - Cc.gx_hi) + (xl - Cc.gx_lo);
+            const float gdy = (y - Cc.gy_hi) + (yl - Cc.gy_lo);
+            const float d2 = fmaf(gdx, gdx, gdy * gdy);
+            if (!done && d2 <= Cc.goal_r2) done = true;
+            J = fmaf(Cc.wg, sqrtf(d2), J);
+        }
+        // fold the low parts back and leave the terrain frame
+        const float xs[13] = {(x + T.x0_hi) + (xl + T.x0_lo), (y + T.y0_hi) + (yl + T.y0_lo),
+                              z + zl, psi + psil, th, ph, vx + vxl, vy + vyl, vz + vzl,
+                              wx, wy, wz, d};
+        bool finite = isfinite(J);
+#pragma unroll
+        for (int c = 0; c < 13; ++c) finite = finite && isfinite(xs[c]);
+        if (!finite) J = CUDART_INF_F;
+        feasible = finite && margin > 0.f;
+        const uint8_t fl = (feasible ? ATP_FLAG_FEASIBLE : 0) | (done ? ATP_FLAG_DONE : 0) |
+                           (off ? ATP_FLAG_OFFMAP : 0) | (finite ? 0 : ATP_FLAG_NONFINITE);
+        if (p.cost) p.cost[j] = J;
+        if (p.margin) p.margin[j] = margin;
+        if (p.flags) p.flags[j] = fl;
+        if (p.xf) {
+            const size_t N = (size_t)p.N;
+#pragma unroll
+            for (int c = 0; c < 13; ++c) p.xf[c * N + j] = xs[c];
+        }
+    }
+
+    if (!REDUCE) return;
+
+    // ---- empirical argmin (Sec. IV-D, reading Q7): min of (infeasible, J, j)
+    __shared__ unsigned long long s_key[kPlanBlock / 32];
+    __shared__ unsigned int s_cnt[kPlanBlock / 32];
+    __shared__ bool s_last;
+    unsigned long long key = ~0ull;
+    if (live)
+        key = ((unsigned long long)(feasible ? 0u : 1u) << 63) |
+              ((unsigned long long)order_u32(J) << 31) | (unsigned long long)j;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other < key ? other : key;
+    }
+    const unsigned int nf = __popc(__ballot_sync(0xffffffffu, live && feasible));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_key[warp] = key;
+        s_cnt[warp] = nf;
+    }
+    __threadfence();          // per-candidate outputs visible before the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bk = s_key[0];
+        unsigned int bc = s_cnt[0];
+        for (int w = 1; w < kPlanBlock / 32; ++w) {
+            bk = s_key[w] < bk ? s_key[w] : bk;
+            bc += s_cnt[w];
+        }
+        atomicMin(&p.scratch->key, bk);
+        atomicAdd(&p.scratch->count, bc);
+        __threadfence();
+        const unsigned int t = atomicAdd(&p.scratch->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+
+    // ---- last CTA: result, best controls and per-step margins, reset scratch
+    __shared__ unsigned long long s_best;
+    __shared__ unsigned int s_nf;
+    __shared__ unsigned long long s_mkey[kPlanBlock];
+    if (threadIdx.x == 0) {
+        s_best = atomicAdd(&p.scratch->key, 0ull);
+        s_nf = atomicAdd(&p.scratch->count, 0u);
+    }
+    __syncthreads();
+    const uint32_t best = (uint32_t)(s_best & 0x7fffffffull);
+    const size_t N = (size_t)p.N;
+    unsigned long long mk = ~0ull;
+    for (int k = threadIdx.x; k < p.H; k += blockDim.x) {
+        const float2 u = __ldcg(p.ctrl + (size_t)k * N + best);
+        if (p.best_ctrl) {
+            p.best_ctrl[2 * k] = clamp_keep_nan(u.x, -V.ddmax, V.ddmax);
+            p.best_ctrl[2 * k + 1] = u.y;
+        }
+        const float m = __ldcg(p.step_margin + (size_t)k * N + best);
+        if (p.best_margin) p.best_margin[k] = m;
+        const unsigned long long c = ((unsigned long long)order_u32(m) << 32) | (unsigned int)k;
+        mk = c < mk ? c : mk;
+    }
+    s_mkey[threadIdx.x] = mk;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < blockDim.x; ++t) mk = s_mkey[t] < mk ? s_mkey[t] : mk;
+        atp_plan_out o;
+        o.best_idx = best;
+        o.n_feasible = s_nf;
+        o.best_cost = __ldcg(p.cost + best);
+        o.best_min_margin = __ldcg(p.margin + best);
+        o.best_min_step = (int32_t)(mk & 0xffffffffull);
+        o.reserved = 0;
+        *p.out = o;
+        // restore the scratch for the next plan on this stream
+        p.scratch->key = ~0ull;
+        p.scratch->count = 0u;
+        p.scratch->ticket = 0u;
+    }
+}
+
+cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
+{
+    const dim3 block(kPlanBlock);
+    const dim3 grid((unsigned)((p.N + kPlanBlock - 1) / kPlanBlock));
+    const bool per = p.x0_soa != nullptr;
+    if (reduce) {
+        if (per) plan_kernel<true, true><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<false, true><<<grid, block, 0, stream>>>(p);
+    } else {
+        if (per) plan_kernel<true, false><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<false, false><<<grid, block, 0, stream>>>(p);
+    }
+    return cudaGetLastError();
+}
+
+// Terrain texels (Sec. III-A numeric slope, reading Q10): height, central-
+// difference slopes (one-sided on the border) and the costmap value.
+__global__ void terrain_prepare_f32_kernel(const float *__restrict__ H, const float *__restrict__ cm,
+                                           int nx, int ny, float inv_cell, float4 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const size_t r = (size_t)j * nx;
+    const float c = H[r + i];
+    float gx, gy;
+    if (i == 0) gx = (H[r + 1] - c) * inv_cell;
+    else if (i == nx - 1) gx = (c - H[r + nx - 2]) * inv_cell;
+    else gx = (H[r + i + 1] - H[r + i - 1]) * (0.5f * inv_cell);
+    if (j == 0) gy = (H[r + nx + i] - c) * inv_cell;
+    else if (j == ny - 1) gy = (c - H[r - nx + i]) * inv_cell;
+    else gy = (H[r + nx + i] - H[r - nx + i]) * (0.5f * inv_cell);
+    out[r + i] = make_float4(c, gx, gy, cm ? cm[r + i] : 0.f);
+}
+
+cudaError_t launch_terrain_prepare_f32(const float *heights, const float *costmap, int nx, int ny,
+                                       float inv_cell, float4 *out, cudaStream_t stream)
+{
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8));
+    terrain_prepare_f32_kernel<<<grid, block, 0, stream>>>(heights, costmap, nx, ny, inv_cell, out);
+    return cudaGetLastError();
+}
+
+}  // namespace atp

@@ -1,0 +1,49 @@
+// plan_kernel.cuh - parameters and launchers of the fused rollout + argmin
+// kernel (arxiv 2603.20525, Sec. IV-A..IV-D).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "atp.h"
+#include "srb_model.cuh"
+
+namespace atp {
+
+// Reduction scratch of one plan: the packed argmin key, the feasible count and
+// the ticket that elects the last CTA.  The last CTA restores the initial
+// values, so consecutive plans on one stream need no memset.
+struct Scratch {
+    unsigned long long key;   // initial ~0ull
+    unsigned int count;       // initial 0
+    unsigned int ticket;      // initial 0
+};
+
+struct PlanParams {
+    Veh V;
+    Cost C;
+    Terrain T;
+    float x0[13];             // shared initial state (x0_soa == nullptr)
+    const float *x0_soa;      // [13][N] per-candidate initial states, or nullptr
+    const float2 *ctrl;       // [H][N]
+    int N, H, n_sub;
+    float h;                  // Euler step dt / n_sub
+    float *cost;              // [N] or nullptr
+    float *margin;            // [N] or nullptr
+    uint8_t *flags;           // [N] or nullptr
+    float *xf;                // [13][N] or nullptr
+    float *step_margin;       // [H][N] or nullptr
+    // plan only
+    atp_plan_out *out;
+    float *best_ctrl;         // [H][2] or nullptr
+    float *best_margin;       // [H] or nullptr
+    Scratch *scratch;
+};
+
+constexpr int kPlanBlock = 64;
+
+cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream);
+cudaError_t launch_terrain_prepare_f32(const float *heights, const float *costmap, int nx, int ny,
+                                       float inv_cell, float4 *out, cudaStream_t stream);
+
+}  // namespace atp

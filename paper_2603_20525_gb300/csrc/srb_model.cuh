@@ -1,0 +1,183 @@
+// srb_model.cuh - FP32 device model of the single-rigid-body (SRB) off-road
+// vehicle of arxiv 2603.20525, Sec. IV-A, with the sigmoid tire of Sec. III-A,
+// the energy stability margin of Sec. IV-B and the running cost of Sec. IV-C.
+//
+// One thread owns one candidate: its state lives in registers for the whole
+// horizon, so a rollout step reads memory only for the four bilinear terrain
+// lookups (16 texels).
+//
+// Precision.  The arithmetic is FP32.  The slowly varying, large-magnitude
+// state components (position, heading and linear velocity) are accumulated as
+// unevaluated sums hi + lo of two floats (Knuth's TwoSum), and positions are
+// kept relative to the terrain origin and split into an integer cell and a
+// fraction before the lookup.  Without that, the rounding of a 20-100 m
+// coordinate (1e-6 m per Euler step) walks the wheels across the terrain by
+// ~1e-5 m over a horizon, which the spring turns into force errors far above
+// the 1e-4 relative agreement with the FP64 oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace atp {
+
+// Vehicle constants in FP32, derived on the host in FP64 (App. B notation).
+struct Veh {
+    float M, halfM, invM;
+    float dJyz, dJxz, dJxy;          // Jyy-Jzz, Jxx-Jzz, Jxx-Jyy
+    float invJxx, invJyy, invJzz;
+    float Lf, Lr, he, hR;            // he = e / 2
+    float kf, kr, bf, br;
+    float Fsf, Fsr;                  // nominal tire loading (g/2) K_zz,i
+    float C, mu, mu2;
+    float dmax, ddmax, g;
+    float MgRbar;                    // M g Rbar
+    float cpb, spb;                  // cos(phibar), sin(phibar)
+    float tip;                       // pi/2 - phibar: roll at which U_ESM = 0
+};
+
+struct Cost {
+    float wt, wc, wg, sigma, inv_eps;
+    float gx_hi, gx_lo, gy_hi, gy_lo;  // goal relative to the terrain origin
+    float goal_r2;
+};
+
+struct Terrain {
+    const float4 *tex;               // (f, f_x, f_y, cost) per node, row-major
+    int nx, ny;
+    float inv_cell;                  // 1 / cell
+    float x0_hi, x0_lo, y0_hi, y0_lo;  // terrain origin
+};
+
+// x + y = s + e exactly (Knuth's TwoSum; no ordering precondition).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// hi + lo += d, renormalised.
+__device__ __forceinline__ void acc2(float &hi, float &lo, float d)
+{
+    float s, e;
+    two_sum(hi, d, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// Energy stability margin (Sec. IV-B): U = +/- M g Rbar (1 - sin(|phi| +
+// phibar)) cos(theta), positive while the CoM is inside the footprint,
+// |phi| < pi/2 - phibar.  sin(|phi| + phibar) is expanded with the already
+// computed sin(phi), cos(phi), so it costs no extra transcendental.
+__device__ __forceinline__ float esm(const Veh &V, float ph, float sph, float cph, float cth)
+{
+    float sabs = ph < 0.f ? -sph : sph;                  // sin(|phi|)
+    float s = fmaf(sabs, V.cpb, cph * V.spb);            // sin(|phi| + phibar)
+    float u = V.MgRbar * (1.f - s) * cth;
+    return fabsf(ph) < V.tip ? u : -u;
+}
+
+// Position of the CoM in cell units split into an integer cell and a
+// fraction, from the compensated coordinate hi + lo (metres from the origin).
+__device__ __forceinline__ void cell_split(float hi, float lo, float inv_cell, int &ic, float &fc)
+{
+    const float u = fminf(fmaxf(hi * inv_cell, -4194304.f), 4194304.f);   // NaN -> low edge
+    const float fl = floorf(u);
+    ic = (int)fl;
+    fc = fmaf(hi, inv_cell, -fl) + lo * inv_cell;
+}
+
+// One axis of a wheel lookup: CoM cell (ic, fc) plus the wheel's offset `o`
+// metres; returns the clamped cell index in [0, n-2] and the weight in [0, 1]
+// (queries clamped to the map, reading Q10).
+__device__ __forceinline__ int axis(int ic, float fc, float o, float inv_cell, int n, float &a, bool &off)
+{
+    const float u = fmaf(o, inv_cell, fc);
+    const float fl = floorf(u);
+    int i = ic + (int)fmaxf(fminf(fl, 4194304.f), -4194304.f);
+    a = u - fl;
+    if (i < 0) {
+        off = true;
+        i = 0;
+        a = 0.f;
+    } else if (i >= n - 1) {
+        if (i > n - 1 || a > 0.f) off = true;
+        i = n - 2;
+        a = 1.f;
+    }
+    return i;
+}
+
+__device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a, float b)
+{
+    const float4 *r0 = T.tex + (size_t)j * T.nx + i;
+    const float4 t00 = __ldg(r0), t10 = __ldg(r0 + 1);
+    const float4 t01 = __ldg(r0 + T.nx), t11 = __ldg(r0 + T.nx + 1);
+    float4 o;
+    float lo, hi;
+    lo = fmaf(a, t10.x - t00.x, t00.x); hi = fmaf(a, t11.x - t01.x, t01.x); o.x = fmaf(b, hi - lo, lo);
+    lo = fmaf(a, t10.y - t00.y, t00.y); hi = fmaf(a, t11.y - t01.y, t01.y); o.y = fmaf(b, hi - lo, lo);
+    lo = fmaf(a, t10.z - t00.z, t00.z); hi = fmaf(a, t11.z - t01.z, t01.z); o.z = fmaf(b, hi - lo, lo);
+    lo = fmaf(a, t10.w - t00.w, t00.w); hi = fmaf(a, t11.w - t01.w, t01.w); o.w = fmaf(b, hi - lo, lo);
+    return o;
+}
+
+// What one wheel contributes to the force and moment sums.
+struct WheelOut {
+    float Fz, Fy, cost;
+};
+
+// Per-step body quantities the four wheels share.
+struct Body {
+    float R[9];
+    int icx, icy;            // CoM cell
+    float fcx, fcy;          // CoM fraction of the cell
+    float z_hi, z_lo;        // CoM height
+    float vx, vy, vz, wx, wy, wz;
+};
+
+// One wheel (Sec. IV-A): contact point P = p + R rho, its body velocity
+// v + w x rho, terrain below it, extension chi and rate against the local
+// slope-normal tau ~ (-f_x, -f_y, 1) (reading Q1), spring and damper with
+// liftoff, slip angle and sigmoid tire force.
+__device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const Body &B,
+                                          float rx, float ry, float k, float b, float Fs,
+                                          float di, bool &off)
+{
+    const float *R = B.R;
+    // offset of the contact point from the CoM in W: R (rx, ry, -(h+R))
+    const float ox = fmaf(rx, R[0], fmaf(ry, R[1], -V.hR * R[2]));
+    const float oy = fmaf(rx, R[3], fmaf(ry, R[4], -V.hR * R[5]));
+    const float oz = fmaf(rx, R[6], fmaf(ry, R[7], -V.hR * R[8]));
+    // body velocity of the contact point: v + w x rho
+    const float vix = B.vx - B.wy * V.hR - B.wz * ry;
+    const float viy = B.vy + B.wz * rx + B.wx * V.hR;
+    const float viz = B.vz + B.wx * ry - B.wy * rx;
+    // terrain below the contact point
+    float a, bb;
+    const int i = axis(B.icx, B.fcx, ox, T.inv_cell, T.nx, a, off);
+    const int j = axis(B.icy, B.fcy, oy, T.inv_cell, T.ny, bb, off);
+    const float4 t = bilerp(T, i, j, a, bb);
+    // tau in B = R^T (-f_x, -f_y, 1)
+    const float tx = R[6] - R[0] * t.y - R[3] * t.z;
+    const float ty = R[7] - R[1] * t.y - R[4] * t.z;
+    const float tz = R[8] - R[2] * t.y - R[5] * t.z;
+    const float itz = 1.f / tz;
+    // P_z - f with the compensated CoM height
+    const float chi = ((B.z_hi - t.x) + (oz + B.z_lo)) * itz;
+    // omega x b_z in B is (w_y, -w_x, 0)
+    const float chid = (tx * (vix - chi * B.wy) + ty * (viy + chi * B.wx) + tz * viz) * itz;
+    const float Fk = fmaxf(Fs - k * chi, 0.f);
+    const float Fz = Fk > 0.f ? fmaxf(Fk - b * chid, 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
+    const float alpha = atan2f(viy, vix) - di;
+    const float Ca = V.C * alpha;
+    const float Fy = Fz * (-Ca * V.mu) * rsqrtf(fmaf(Ca, Ca, V.mu2));
+    WheelOut w;
+    w.Fz = Fz;
+    w.Fy = Fy;
+    w.cost = t.w;
+    return w;
+}
+
+}  // namespace atp

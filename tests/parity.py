@@ -1,0 +1,109 @@
+"""Shared parity protocol of the GPU-vs-oracle tests.
+
+Error measure: per field |g - o| / max(|o|, floor), floors 1 m (positions),
+0.01 rad (angles), 0.1 m/s, 0.1 rad/s, 1 cost unit and 1 % of the level-ground
+ESM; a candidate's error is the largest over cost, margin and final state.
+
+Bar: TOL = 1e-4, the FP32-vs-FP64 tolerance.  The rough-terrain rollout is
+not equally well conditioned everywhere: nudging the FP32 initial state by one
+ulp (relative 6e-8) already moves the exact FP64 result by 1e-5 for a typical
+candidate and by far more for some, which no FP32 arithmetic can undercut.  So
+each candidate's conditioning is measured on the oracle itself (`sens`, the
+largest change over N_NUDGES one-ulp nudges of its inputs) and the GPU must
+agree to within max(TOL, KAPPA * sens).  The nudges move every component of
+the initial state and every control by one ulp in a random direction, the way
+FP32 rounding perturbs every quantity at once.
+
+Reported, not asserted: candidates the oracle finds infeasible (their roll has
+crossed the tipping point of the ESM, beyond which the fall diverges
+exponentially; only the feasibility bit is compared for them), and candidates
+that pass within reach of FP32 rounding of a discontinuity of the method (a
+wheel touching down while compressing, where the damper force jumps from 0;
+the goal circle; U_ESM = 0, which decides feasibility).
+"""
+import math
+
+import numpy as np
+
+TOL = 1e-4
+KAPPA = 20.0
+STATE_FLOORS = np.array([1.0, 1.0, 1.0, 0.01, 0.01, 0.01, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.01])
+COST_FLOOR = 1.0
+# distances to a switch (as normalised by the oracle's diag output) below which
+# FP32 and FP64 may take different branches
+TAU_CONTACT = 1e-4      # |F_s - k chi| / F_s
+TAU_ESM = 1e-4          # |U| / U0
+TAU_GOAL = 1e-4         # | |p - goal| - r_g |  [m]
+N_NUDGES = 6
+
+
+def level_esm(veh):
+    Rb = math.hypot(veh["hR"], 0.5 * veh["e"])
+    return veh["M"] * veh["g"] * (Rb - veh["hR"])
+
+
+def branch_sensitive(diag):
+    return (diag[:, 0] < TAU_CONTACT) | (diag[:, 1] < TAU_ESM) | (diag[:, 2] < TAU_GOAL)
+
+
+def rel(g, o, floor):
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    with np.errstate(invalid="ignore"):
+        same_inf = np.isinf(g) & np.isinf(o) & (np.sign(g) == np.sign(o))
+        e = np.abs(g - o) / np.maximum(np.abs(o), floor)
+    e = np.where(same_inf, 0.0, e)
+    return np.where(np.isnan(e), np.inf, e)
+
+
+def compare(gpu: dict, orc: dict, veh: dict):
+    """Per-candidate max relative error over cost, margin and final state."""
+    U0 = level_esm(veh)
+    eJ = rel(gpu["cost"], orc["J"], COST_FLOOR)
+    eM = rel(gpu["margin"], orc["margin"], 0.01 * U0)
+    err = np.maximum(eJ, eM)
+    eX = None
+    if gpu.get("xf") is not None and orc.get("xf") is not None:
+        eX = rel(gpu["xf"], orc["xf"], STATE_FLOORS[None, :])
+        err = np.maximum(err, eX.max(axis=1))
+    return dict(err=err, eJ=eJ, eM=eM, eX=eX)
+
+
+def nudge(a, rng):
+    """Every element of an FP32 array moved by one ulp, random direction."""
+    a = np.asarray(a, dtype=np.float32)
+    up = rng.integers(0, 2, size=a.shape).astype(bool)
+    return np.nextafter(a, np.where(up, np.float32(np.inf), np.float32(-np.inf))).astype(np.float32)
+
+
+def conditioning(oracle, veh, cost, ter, x0, ctrl, dt, n_sub, base, seed=0):
+    """Largest per-candidate change of the FP64 result over N_NUDGES one-ulp
+    nudges of the initial state(s) and the controls."""
+    rng = np.random.default_rng(seed)
+    sens = np.zeros(len(base["J"]))
+    for _ in range(N_NUDGES):
+        r = oracle.rollout(veh, cost, ter, nudge(x0, rng), nudge(ctrl, rng), dt, n_sub)
+        c = compare(dict(cost=r["J"], margin=r["margin"], xf=r["xf"]), base, veh)
+        sens = np.maximum(sens, c["err"])
+    return sens
+
+
+def classify(gpu: dict, orc: dict, sens, veh: dict):
+    """Per-candidate verdict.  Returns a dict of boolean masks and stats."""
+    c = compare(gpu, orc, veh)
+    err = c["err"]
+    feas = (orc["flags"] & 1) > 0
+    branch = branch_sensitive(orc["diag"])
+    bound = np.maximum(TOL, KAPPA * sens)
+    checked = feas & ~branch
+    ok = err <= bound
+    strict = err <= TOL
+    stats = dict(n=len(err), feasible=int(feas.sum()), branch=int((feas & branch).sum()),
+                 checked=int(checked.sum()),
+                 strict_frac=float(strict[checked].mean()) if checked.any() else 1.0,
+                 max_err_checked=float(err[checked].max()) if checked.any() else 0.0,
+                 worst_ratio=float(np.nan_to_num(err / bound)[checked].max()) if checked.any() else 0.0,
+                 median_err=float(np.median(err[checked])) if checked.any() else 0.0,
+                 median_sens=float(np.median(sens[checked])) if checked.any() else 0.0)
+    return dict(err=err, bound=bound, feas=feas, branch=branch, checked=checked, ok=ok,
+                strict=strict, stats=stats, cmp=c)
