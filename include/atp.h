@@ -192,6 +192,31 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
                 float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
                 float *cand_xf_dev, float *step_margin_dev, void *stream);
 
+/* Plan without allocating: atp_plan for callers that cannot allocate device
+ * memory once running, such as a planner in a hard real-time control loop
+ * whose latency budget or certification forbids cudaMalloc after start-up, or
+ * a plugin host that gives its plugins no allocator.  The paper has no
+ * counterpart; it exists for such callers only.
+ *
+ * Arguments, outputs and results are those of atp_plan, without a context.
+ * Its scratch is one file-scope device array of 8 MiB in this library, which
+ * every GPU that loads the library holds until the process exits.  It
+ * supports plans whose scratch (256 B + 9 N bytes + 4 N H bytes, each part
+ * rounded up to 256 B) fits in 8 MiB, e.g. N = 16384 with H <= 125; larger
+ * plans return ATP_ERR_UNSUPPORTED before anything is enqueued.  The call
+ * runs on the calling thread's current device (at most device 63), calls no
+ * cudaMalloc or cudaFree, and enqueues two small memsets that reset the
+ * reduction state before the kernel.  Its first call on a device looks up the
+ * array's device address with that device current (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the one
+ * array, so calls that overlap on the GPU (other streams, other host threads)
+ * race and corrupt each other's results: serialise them. */
+int atp_plan_noalloc(const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
+                     const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int N,
+                     int H, float dt, int n_sub, atp_plan_out *out_dev, float *best_ctrl_dev,
+                     float *best_margin_dev, float *cand_cost_dev, float *cand_margin_dev,
+                     uint8_t *cand_flags_dev, float *cand_xf_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "atp.h"
@@ -404,3 +405,83 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Plan without allocation.  Some callers cannot allocate device memory once
+// they are running, for example a planner in a hard real-time control loop
+// whose latency budget or certification forbids cudaMalloc after start-up,
+// or a plugin host that gives its plugins no allocator.  atp_plan_noalloc
+// runs the same kernel as atp_plan, but its scratch is the file-scope array
+// below, which every GPU that loads this library holds until the process ends.
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 8u << 20;   // 8 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_plan_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices];
+
+// Device address of g_plan_scratch on the current device.  Host code only
+// sees a host-side stand-in for the array's name, so the address is looked up
+// once per device with that device current.
+int noalloc_scratch(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_plan_scratch) != cudaSuccess || !p) return ATP_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ATP_OK;
+}
+
+}  // namespace
+
+extern "C" int atp_plan_noalloc(const atp_vehicle *veh, const atp_cost *cost,
+                                const atp_terrain *terrain, const atp_state *x0,
+                                const float *x0_dev, const float *ctrl_dev, int N, int H,
+                                float dt, int n_sub, atp_plan_out *out_dev, float *best_ctrl_dev,
+                                float *best_margin_dev, float *cand_cost_dev,
+                                float *cand_margin_dev, uint8_t *cand_flags_dev,
+                                float *cand_xf_dev, void *stream)
+{
+    int ns = 0;
+    int rc = common_checks(nullptr, veh, cost, terrain, x0, x0_dev, ctrl_dev, N, H, dt, n_sub, &ns);
+    if (rc != ATP_OK) return rc;
+    if (!out_dev) return ATP_ERR_INVALID;
+    const ScratchLayout L = layout((size_t)N, (size_t)H);
+    if (L.total > kNoallocScratchBytes) return ATP_ERR_UNSUPPORTED;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return ATP_ERR_CUDA;
+    if (dev >= kMaxDevices) return ATP_ERR_UNSUPPORTED;
+    void *scratch = nullptr;
+    if ((rc = noalloc_scratch(dev, &scratch)) != ATP_OK) return rc;
+    char *base = (char *)scratch;
+    // the reduction key starts at all ones, the count and ticket at zero; the
+    // kernel's last CTA leaves them so, but a fresh process or an earlier
+    // failed launch may not have
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(base, 0xff, sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMemsetAsync(base + sizeof(unsigned long long), 0,
+                        sizeof(atp::Scratch) - sizeof(unsigned long long), s) != cudaSuccess)
+        return ATP_ERR_CUDA;
+    atp::PlanParams p;
+    std::memset(&p, 0, sizeof p);
+    derive(*veh, *cost, *terrain, p);
+    fill_problem(p, x0, x0_dev, ctrl_dev, N, H, dt, ns);
+    p.cost = cand_cost_dev ? cand_cost_dev : (float *)(base + L.cost);
+    p.margin = cand_margin_dev ? cand_margin_dev : (float *)(base + L.margin);
+    p.flags = cand_flags_dev ? cand_flags_dev : (uint8_t *)(base + L.flags);
+    p.xf = cand_xf_dev;
+    p.step_margin = (float *)(base + L.step_margin);
+    p.out = out_dev;
+    p.best_ctrl = best_ctrl_dev;
+    p.best_margin = best_margin_dev;
+    p.scratch = (atp::Scratch *)base;
+    if (atp::launch_plan(p, true, s) != cudaSuccess) return ATP_ERR_CUDA;
+    return ATP_OK;
+}
