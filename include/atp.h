@@ -192,6 +192,13 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
                 float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
                 float *cand_xf_dev, float *step_margin_dev, void *stream);
 
+/* Diagnostic: evaluates the library's own FP32 elementary functions next to
+ * CUDA's on n input pairs (a_i, b_i), writing 8 floats per pair to out_dev:
+ * [sin a, cos a] (library), [sinf a, cosf a] (CUDA), atan2(a, b) (library),
+ * atan2f(a, b) (CUDA), 1/b (library reciprocal), 1.0f/b (IEEE division).
+ * All pointers are device memory of n (a, b) and 8 n (out) floats. */
+int atp_math_check(const float *a_dev, const float *b_dev, int n, float *out_dev, void *stream);
+
 /* Plan without allocating: atp_plan for callers that cannot allocate device
  * memory once running, such as a planner in a hard real-time control loop
  * whose latency budget or certification forbids cudaMalloc after start-up, or

@@ -25,7 +25,7 @@ FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
 # every symbol include/atp.h declares
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
-           "atp_plan_noalloc")
+           "atp_plan_noalloc", "atp_math_check")
 
 
 class Vehicle(C.Structure):
@@ -92,8 +92,9 @@ def load(build_if_missing: bool = True):
         L.atp_plan_noalloc.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
                                        C.POINTER(State), _vp, _vp, C.c_int, C.c_int, C.c_float,
                                        C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.atp_math_check.argtypes = [_vp, _vp, C.c_int, _vp, _vp]
         for n in ("atp_create", "atp_destroy", "atp_reserve", "atp_terrain_prepare",
-                  "atp_plan", "atp_rollout", "atp_plan_noalloc"):
+                  "atp_plan", "atp_rollout", "atp_plan_noalloc", "atp_math_check"):
             getattr(L, n).restype = C.c_int
         _lib = L
         return L

@@ -1,0 +1,91 @@
+// fastmath.cuh - the FP32 elementary functions of the rollout, written for the
+// argument ranges the SRB model produces, each a few FMAs instead of a general
+// library sequence.  Accuracy against CUDA's own functions is checked on the
+// GPU by tests/test_gpu_math.py (atp_math_check).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace atp {
+
+// Single MUFU reciprocal (rcp.approx.f32, max error 1 ulp).
+__device__ __forceinline__ float rcp(float x)
+{
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// sin and cos of |x| <= pi/4 from their Taylor series, truncated after x^11
+// and x^12: the first omitted terms are below 7e-12 and 2e-13 on the interval.
+__device__ __forceinline__ void sincos_q(float x, float &s, float &c)
+{
+    const float x2 = x * x;
+    float ps = fmaf(x2, -2.50521084e-08f, 2.75573192e-06f);    // -1/11!, 1/9!
+    ps = fmaf(x2, ps, -1.98412698e-04f);                        // -1/7!
+    ps = fmaf(x2, ps, 8.33333333e-03f);                         //  1/5!
+    ps = fmaf(x2, ps, -1.66666667e-01f);                        // -1/3!
+    s = fmaf(x * x2, ps, x);
+    float pc = fmaf(x2, 2.08767570e-09f, -2.75573192e-07f);     // 1/12!, -1/10!
+    pc = fmaf(x2, pc, 2.48015873e-05f);                         //  1/8!
+    pc = fmaf(x2, pc, -1.38888889e-03f);                        // -1/6!
+    pc = fmaf(x2, pc, 4.16666667e-02f);                         //  1/4!
+    pc = fmaf(x2, pc, -0.5f);                                   // -1/2!
+    c = fmaf(x2, pc, 1.0f);
+}
+
+// sin and cos of any |x| < 2^17: Cody-Waite reduction by pi/2, split into
+// three floats (pi/2 = P1 + P2 + P3 to 72 bits), then the quadrant's
+// polynomial.  Larger or non-finite arguments take CUDA's sincosf.
+__device__ __forceinline__ void sincos_r(float x, float &s, float &c)
+{
+    if (fabsf(x) <= 0.785398163f) {
+        sincos_q(x, s, c);
+        return;
+    }
+    if (!(fabsf(x) < 131072.f)) {
+        sincosf(x, &s, &c);
+        return;
+    }
+    const float k = rintf(x * 6.36619747e-01f);                 // x / (pi/2)
+    float r = fmaf(-k, 1.57079637e+00f, x);                     // P1 = fl(pi/2)
+    r = fmaf(-k, -4.37113883e-08f, r);                          // P2 = fl(pi/2 - P1)
+    r = fmaf(-k, -1.71512451e-15f, r);                          // P3 = fl(pi/2 - P1 - P2)
+    float sr, cr;
+    sincos_q(r, sr, cr);
+    const int q = ((int)k) & 3;
+    s = (q == 0) ? sr : (q == 1) ? cr : (q == 2) ? -sr : -cr;
+    c = (q == 0) ? cr : (q == 1) ? -sr : (q == 2) ? -cr : sr;
+}
+
+// atan(r) for r in [0, 1] as r P(r^2), P of degree 8 fitted for minimum
+// maximum relative error (fit_atan.py): 1.1e-7 including FP32 evaluation.
+__device__ __forceinline__ float atan01(float r)
+{
+    const float s = r * r;
+    float p = fmaf(s, 0.0028498878236860037f, -0.016068624332547188f);
+    p = fmaf(s, p, 0.04269151762127876f);
+    p = fmaf(s, p, -0.07504294812679291f);
+    p = fmaf(s, p, 0.10640934109687805f);
+    p = fmaf(s, p, -0.14203645288944244f);
+    p = fmaf(s, p, 0.1999261975288391f);
+    p = fmaf(s, p, -0.3333307206630707f);
+    p = fmaf(s, p, 1.0f);
+    return r * p;
+}
+
+// atan2(y, x) by octant reduction to atan01; atan2(+-0, +-0) = 0 like the
+// FP64 oracle's libm for x = +0, and NaN propagates.
+__device__ __forceinline__ float atan2_r(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float r = mx > 0.f ? mn * rcp(mx) : mn;
+    float t = atan01(r);
+    if (ay > ax) t = 1.57079633f - t;
+    if (x < 0.f) t = 3.14159265f - t;
+    t = copysignf(t, y);
+    return (x != x || y != y) ? x + y : t;
+}
+
+}  // namespace atp

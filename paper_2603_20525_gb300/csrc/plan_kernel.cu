@@ -30,41 +30,65 @@ __device__ __forceinline__ float clamp_keep_nan(float v, float lo, float hi)
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
-template <bool PER_X0, bool REDUCE>
+// Sum of v over the four lanes of a candidate's quad (xor butterfly: every
+// lane ends with the same bits, (a0 + a1) + (a2 + a3) in each).
+__device__ __forceinline__ float quad_sum(float v, unsigned mask)
+{
+    v += __shfl_xor_sync(mask, v, 1);
+    v += __shfl_xor_sync(mask, v, 2);
+    return v;
+}
+
+// One candidate per LANES consecutive threads.  LANES = 1: a thread runs all
+// four wheels.  LANES = 4: lane q of the quad runs wheel q (fl, fr, rl, rr)
+// and the body-level arithmetic is repeated bit-identically on all four, so
+// the quad never needs to exchange state, only the five force/moment sums
+// and the costmap sum (two shuffles each).
+template <int LANES, bool PER_X0, bool REDUCE>
 __global__ void __launch_bounds__(kPlanBlock)
 plan_kernel(const __grid_constant__ PlanParams p)
 {
     const Veh &V = p.V;
     const Cost &Cc = p.C;
     const Terrain &T = p.T;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = tid / LANES;
+    const int q = LANES == 1 ? 0 : (tid & (LANES - 1));
     const bool live = j < p.N;
+    const unsigned qmask = LANES == 1 ? 0u : (0xfu << (threadIdx.x & 28));
 
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
 
     if (live) {
+        // this lane's wheel (LANES = 4)
+        const bool front = q < 2;
+        const float wrx = front ? V.Lf : -V.Lr;
+        const float wry = (q & 1) ? -V.he : V.he;
+        const float wk = front ? V.kf : V.kr;
+        const float wb = front ? V.bf : V.br;
+        const float wFs = front ? V.Fsf : V.Fsr;
         // state; x, y relative to the terrain origin; *_l are the low parts of
         // the compensated components
         float x, xl, y, yl, z, zl, psi, psil, vx, vxl, vy, vyl, vz, vzl;
         float th, ph, wx, wy, wz, d;
         {
-            float q[13];
+            float x0[13];
             if (PER_X0) {
                 const size_t N = (size_t)p.N;
 #pragma unroll
-                for (int c = 0; c < 13; ++c) q[c] = p.x0_soa[c * N + j];
+                for (int c = 0; c < 13; ++c) x0[c] = p.x0_soa[c * N + j];
             } else {
 #pragma unroll
-                for (int c = 0; c < 13; ++c) q[c] = p.x0[c];
+                for (int c = 0; c < 13; ++c) x0[c] = p.x0[c];
             }
-            two_sum(q[0], -T.x0_hi, x, xl);
+            two_sum(x0[0], -T.x0_hi, x, xl);
             xl -= T.x0_lo;
-            two_sum(q[1], -T.y0_hi, y, yl);
+            two_sum(x0[1], -T.y0_hi, y, yl);
             yl -= T.y0_lo;
-            z = q[2]; psi = q[3]; th = q[4]; ph = q[5];
-            vx = q[6]; vy = q[7]; vz = q[8];
-            wx = q[9]; wy = q[10]; wz = q[11]; d = q[12];
+            z = x0[2]; psi = x0[3]; th = x0[4]; ph = x0[5];
+            vx = x0[6]; vy = x0[7]; vz = x0[8];
+            wx = x0[9]; wy = x0[10]; wz = x0[11]; d = x0[12];
             zl = psil = vxl = vyl = vzl = 0.f;
         }
         bool done = false, off = false;
@@ -77,15 +101,15 @@ plan_kernel(const __grid_constant__ PlanParams p)
             const float dd = clamp_keep_nan(u.x, -V.ddmax, V.ddmax);
             const float ax = u.y;
             float sm = CUDART_INF_F;
-            for (int q = 0; q < p.n_sub; ++q) {
+            for (int sub = 0; sub < p.n_sub; ++sub) {
                 if (done) {            // frozen at the goal: the same state each step
                     sm = fminf(sm, Ufrozen);
                     continue;
                 }
                 float sps, cps, sth, cth, sph, cph;
-                sincosf(psi, &sps, &cps);
-                sincosf(th, &sth, &cth);
-                sincosf(ph, &sph, &cph);
+                sincos_r(psi, sps, cps);
+                sincos_r(th, sth, cth);
+                sincos_r(ph, sph, cph);
                 const float U = esm(V, ph, sph, cph, cth);
                 margin = fminf(margin, U);
                 sm = fminf(sm, U);
@@ -117,27 +141,42 @@ plan_kernel(const __grid_constant__ PlanParams p)
                 B.wx = wx; B.wy = wy; B.wz = wz;
                 // gravity in B: R^T (0, 0, -g)
                 const float gBx = -V.g * R[6], gBy = -V.g * R[7], gBz = -V.g * R[8];
-                const WheelOut fl = wheel(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, off);
-                const WheelOut fr = wheel(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, off);
-                const WheelOut rl = wheel(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, off);
-                const WheelOut rr = wheel(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, off);
-                // summed forces and moments; rear longitudinal constraint force
-                const float cd = cosf(d);
-                const float Fyf = (fl.Fy + fr.Fy) * cd;
-                const float Fyr = rl.Fy + rr.Fy;
-                const float FyB = Fyf + Fyr;
-                const float FzB = (fl.Fz + fr.Fz) + (rl.Fz + rr.Fz);
+                float sd, cd;
+                sincos_r(d, sd, cd);
+                // summed forces and moments (Sec. IV-A); the rear
+                // longitudinal constraint force enters My only
+                float FyB, FzB, Mx, My, Mz, csum;
+                if (LANES == 1) {
+                    const WheelOut fl = wheel(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, off);
+                    const WheelOut fr = wheel(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, off);
+                    const WheelOut rl = wheel(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                    const WheelOut rr = wheel(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                    const float Fyf = (fl.Fy + fr.Fy) * cd;
+                    const float Fyr = rl.Fy + rr.Fy;
+                    FyB = Fyf + Fyr;
+                    FzB = (fl.Fz + fr.Fz) + (rl.Fz + rr.Fz);
+                    Mx = V.he * ((fl.Fz - fr.Fz) + (rl.Fz - rr.Fz)) + V.hR * FyB;
+                    My = V.Lr * (rl.Fz + rr.Fz) - V.Lf * (fl.Fz + fr.Fz);
+                    Mz = V.Lf * Fyf - V.Lr * Fyr;
+                    csum = (fl.cost + fr.cost) + (rl.cost + rr.cost);
+                } else {
+                    const WheelOut w = wheel(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, off);
+                    const float fy = front ? w.Fy * cd : w.Fy;
+                    FyB = quad_sum(fy, qmask);
+                    FzB = quad_sum(w.Fz, qmask);
+                    Mx = quad_sum(wry * w.Fz, qmask) + V.hR * FyB;
+                    My = quad_sum(-wrx * w.Fz, qmask);
+                    Mz = quad_sum(wrx * fy, qmask);
+                    csum = quad_sum(w.cost, qmask);
+                }
                 const float Fx = V.halfM * (ax - gBx + wy * vz - wz * vy);
-                const float Mx = V.he * ((fl.Fz - fr.Fz) + (rl.Fz - rr.Fz)) + V.hR * FyB;
-                const float My = -V.hR * (2.f * Fx) - V.Lf * (fl.Fz + fr.Fz) + V.Lr * (rl.Fz + rr.Fz);
-                const float Mz = V.Lf * Fyf - V.Lr * Fyr;
+                My = fmaf(-V.hR, 2.f * Fx, My);
                 // running cost L = L_0 + L_soft (Sec. IV-C), left Riemann sum
                 const float soft = fmaxf(1.f - U * Cc.inv_eps, 0.f);
-                const float L = Cc.wt + Cc.wc * dd * dd + Cc.sigma * soft * soft +
-                                ((fl.cost + fr.cost) + (rl.cost + rr.cost));
+                const float L = Cc.wt + Cc.wc * dd * dd + Cc.sigma * soft * soft + csum;
                 J = fmaf(h, L, J);
                 // state derivative A(xi) + B zeta (Sec. IV-A)
-                const float ic = 1.f / cth;
+                const float ic = rcp(cth);
                 const float wsc = sph * wy + cph * wz;
                 const float dx = R[0] * vx + R[1] * vy + R[2] * vz;
                 const float dy = R[3] * vx + R[4] * vy + R[5] * vz;
@@ -165,16 +204,20 @@ plan_kernel(const __grid_constant__ PlanParams p)
                 wz = fmaf(h, dwz, wz);
                 d = clamp_keep_nan(fmaf(h, dd, d), -V.dmax, V.dmax);
             }
-            if (p.step_margin) p.step_margin[(size_t)k * p.N + j] = sm;
+            if (p.step_margin && q == 0) p.step_margin[(size_t)k * p.N + j] = sm;
+        }
+        if (LANES == 4) {
+            // the off-map flag is per wheel: OR it over the quad
+            off = __any_sync(qmask, off);
         }
         // final state: margin, goal test, terminal cost Phi (Sec. IV-C)
         {
             float sth, cth, sph, cph;
-            sincosf(th, &sth, &cth);
-            sincosf(ph, &sph, &cph);
+            sincos_r(th, sth, cth);
+            sincos_r(ph, sph, cph);
             const float U = esm(V, ph, sph, cph, cth);
             margin = fminf(margin, U);
-            if (p.step_margin) {
+            if (p.step_margin && q == 0) {
                 float *e = p.step_margin + (size_t)(p.H - 1) * p.N + j;
                 *e = fminf(*e, U);
             }
@@ -193,15 +236,17 @@ plan_kernel(const __grid_constant__ PlanParams p)
         for (int c = 0; c < 13; ++c) finite = finite && isfinite(xs[c]);
         if (!finite) J = CUDART_INF_F;
         feasible = finite && margin > 0.f;
-        const uint8_t fl = (feasible ? ATP_FLAG_FEASIBLE : 0) | (done ? ATP_FLAG_DONE : 0) |
-                           (off ? ATP_FLAG_OFFMAP : 0) | (finite ? 0 : ATP_FLAG_NONFINITE);
-        if (p.cost) p.cost[j] = J;
-        if (p.margin) p.margin[j] = margin;
-        if (p.flags) p.flags[j] = fl;
-        if (p.xf) {
-            const size_t N = (size_t)p.N;
+        if (q == 0) {
+            const uint8_t fl = (feasible ? ATP_FLAG_FEASIBLE : 0) | (done ? ATP_FLAG_DONE : 0) |
+                               (off ? ATP_FLAG_OFFMAP : 0) | (finite ? 0 : ATP_FLAG_NONFINITE);
+            if (p.cost) p.cost[j] = J;
+            if (p.margin) p.margin[j] = margin;
+            if (p.flags) p.flags[j] = fl;
+            if (p.xf) {
+                const size_t N = (size_t)p.N;
 #pragma unroll
-            for (int c = 0; c < 13; ++c) p.xf[c * N + j] = xs[c];
+                for (int c = 0; c < 13; ++c) p.xf[c * N + j] = xs[c];
+            }
         }
     }
 
@@ -211,8 +256,9 @@ plan_kernel(const __grid_constant__ PlanParams p)
     __shared__ unsigned long long s_key[kPlanBlock / 32];
     __shared__ unsigned int s_cnt[kPlanBlock / 32];
     __shared__ bool s_last;
+    const bool leader = live && q == 0;
     unsigned long long key = ~0ull;
-    if (live)
+    if (leader)
         key = ((unsigned long long)(feasible ? 0u : 1u) << 63) |
               ((unsigned long long)order_u32(J) << 31) | (unsigned long long)j;
 #pragma unroll
@@ -220,7 +266,7 @@ plan_kernel(const __grid_constant__ PlanParams p)
         unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
         key = other < key ? other : key;
     }
-    const unsigned int nf = __popc(__ballot_sync(0xffffffffu, live && feasible));
+    const unsigned int nf = __popc(__ballot_sync(0xffffffffu, leader && feasible));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         s_key[warp] = key;
@@ -286,19 +332,35 @@ plan_kernel(const __grid_constant__ PlanParams p)
     }
 }
 
-cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
+template <int LANES>
+static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t stream)
 {
     const dim3 block(kPlanBlock);
-    const dim3 grid((unsigned)((p.N + kPlanBlock - 1) / kPlanBlock));
+    const size_t threads = (size_t)p.N * LANES;
+    const dim3 grid((unsigned)((threads + kPlanBlock - 1) / kPlanBlock));
     const bool per = p.x0_soa != nullptr;
     if (reduce) {
-        if (per) plan_kernel<true, true><<<grid, block, 0, stream>>>(p);
-        else plan_kernel<false, true><<<grid, block, 0, stream>>>(p);
+        if (per) plan_kernel<LANES, true, true><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<LANES, false, true><<<grid, block, 0, stream>>>(p);
     } else {
-        if (per) plan_kernel<true, false><<<grid, block, 0, stream>>>(p);
-        else plan_kernel<false, false><<<grid, block, 0, stream>>>(p);
+        if (per) plan_kernel<LANES, true, false><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<LANES, false, false><<<grid, block, 0, stream>>>(p);
     }
     return cudaGetLastError();
+}
+
+int plan_lanes(int N)
+{
+    // four lanes per candidate while the batch leaves the GPU's thread
+    // slots mostly empty (the rollout is then latency bound); one lane when
+    // the batch alone fills the machine
+    return N <= kLanes4MaxN ? 4 : 1;
+}
+
+cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
+{
+    return plan_lanes(p.N) == 4 ? launch_lanes<4>(p, reduce, stream)
+                                : launch_lanes<1>(p, reduce, stream);
 }
 
 // Terrain texels (Sec. III-A numeric slope, reading Q10): height, central-

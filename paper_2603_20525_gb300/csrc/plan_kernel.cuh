@@ -41,7 +41,10 @@ struct PlanParams {
 };
 
 constexpr int kPlanBlock = 64;
+// largest batch that runs four lanes (one wheel each) per candidate
+constexpr int kLanes4MaxN = 1 << 17;
 
+int plan_lanes(int N);
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream);
 cudaError_t launch_terrain_prepare_f32(const float *heights, const float *costmap, int nx, int ny,
                                        float inv_cell, float4 *out, cudaStream_t stream);

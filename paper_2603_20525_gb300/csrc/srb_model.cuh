@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fastmath.cuh"
+
 namespace atp {
 
 // Vehicle constants in FP32, derived on the host in FP64 (App. B notation).
@@ -163,14 +165,14 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     const float tx = R[6] - R[0] * t.y - R[3] * t.z;
     const float ty = R[7] - R[1] * t.y - R[4] * t.z;
     const float tz = R[8] - R[2] * t.y - R[5] * t.z;
-    const float itz = 1.f / tz;
+    const float itz = rcp(tz);
     // P_z - f with the compensated CoM height
     const float chi = ((B.z_hi - t.x) + (oz + B.z_lo)) * itz;
     // omega x b_z in B is (w_y, -w_x, 0)
     const float chid = (tx * (vix - chi * B.wy) + ty * (viy + chi * B.wx) + tz * viz) * itz;
     const float Fk = fmaxf(Fs - k * chi, 0.f);
     const float Fz = Fk > 0.f ? fmaxf(Fk - b * chid, 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
-    const float alpha = atan2f(viy, vix) - di;
+    const float alpha = atan2_r(viy, vix) - di;
     const float Ca = V.C * alpha;
     const float Fy = Fz * (-Ca * V.mu) * rsqrtf(fmaf(Ca, Ca, V.mu2));
     WheelOut w;

@@ -14,12 +14,14 @@ agree to within max(TOL, KAPPA * sens).  The nudges move every component of
 the initial state and every control by one ulp in a random direction, the way
 FP32 rounding perturbs every quantity at once.
 
-Reported, not asserted: candidates the oracle finds infeasible (their roll has
+Every feasible candidate is held to that bound.  The exceptions, counted and
+capped at 1 % of the feasible candidates, are misses by candidates that pass
+within FP32 reach of a discontinuity of the method: a wheel touching down
+while compressing, where the damper force jumps from 0 (reach: K_SWITCH times
+the candidate's conditioning, at least 1e-4 of the preload); U_ESM = 0, which
+decides feasibility; the goal circle.  Infeasible candidates (their roll
 crossed the tipping point of the ESM, beyond which the fall diverges
-exponentially; only the feasibility bit is compared for them), and candidates
-that pass within reach of FP32 rounding of a discontinuity of the method (a
-wheel touching down while compressing, where the damper force jumps from 0;
-the goal circle; U_ESM = 0, which decides feasibility).
+exponentially) are compared on their feasibility bit only.
 """
 import math
 
@@ -31,7 +33,8 @@ STATE_FLOORS = np.array([1.0, 1.0, 1.0, 0.01, 0.01, 0.01, 0.1, 0.1, 0.1, 0.1, 0.
 COST_FLOOR = 1.0
 # distances to a switch (as normalised by the oracle's diag output) below which
 # FP32 and FP64 may take different branches
-TAU_CONTACT = 1e-4      # |F_s - k chi| / F_s
+TAU_CONTACT = 1e-4      # |F_s - k chi| / F_s, at least
+K_SWITCH = 10.0         # x the candidate's conditioning
 TAU_ESM = 1e-4          # |U| / U0
 TAU_GOAL = 1e-4         # | |p - goal| - r_g |  [m]
 N_NUDGES = 6
@@ -42,8 +45,9 @@ def level_esm(veh):
     return veh["M"] * veh["g"] * (Rb - veh["hR"])
 
 
-def branch_sensitive(diag):
-    return (diag[:, 0] < TAU_CONTACT) | (diag[:, 1] < TAU_ESM) | (diag[:, 2] < TAU_GOAL)
+def branch_sensitive(diag, sens=None):
+    reach = TAU_CONTACT if sens is None else np.maximum(TAU_CONTACT, K_SWITCH * np.nan_to_num(sens, nan=np.inf))
+    return (diag[:, 0] < reach) | (diag[:, 1] < TAU_ESM) | (diag[:, 2] < TAU_GOAL)
 
 
 def rel(g, o, floor):
@@ -93,17 +97,19 @@ def classify(gpu: dict, orc: dict, sens, veh: dict):
     c = compare(gpu, orc, veh)
     err = c["err"]
     feas = (orc["flags"] & 1) > 0
-    branch = branch_sensitive(orc["diag"])
-    bound = np.maximum(TOL, KAPPA * sens)
-    checked = feas & ~branch
+    near = branch_sensitive(orc["diag"], sens)
+    bound = np.maximum(TOL, KAPPA * np.nan_to_num(sens, nan=np.inf))
     ok = err <= bound
     strict = err <= TOL
-    stats = dict(n=len(err), feasible=int(feas.sum()), branch=int((feas & branch).sum()),
-                 checked=int(checked.sum()),
-                 strict_frac=float(strict[checked].mean()) if checked.any() else 1.0,
-                 max_err_checked=float(err[checked].max()) if checked.any() else 0.0,
+    fail = feas & ~ok & ~near          # must be empty
+    flipped = feas & ~ok & near        # took the other side of a switch
+    checked = feas & ~flipped
+    stats = dict(n=len(err), feasible=int(feas.sum()), switch_misses=int(flipped.sum()),
+                 fails=int(fail.sum()),
+                 strict_frac=float(strict[feas].mean()) if feas.any() else 1.0,
+                 max_err=float(err[checked].max()) if checked.any() else 0.0,
                  worst_ratio=float(np.nan_to_num(err / bound)[checked].max()) if checked.any() else 0.0,
-                 median_err=float(np.median(err[checked])) if checked.any() else 0.0,
-                 median_sens=float(np.median(sens[checked])) if checked.any() else 0.0)
-    return dict(err=err, bound=bound, feas=feas, branch=branch, checked=checked, ok=ok,
-                strict=strict, stats=stats, cmp=c)
+                 median_err=float(np.median(err[feas])) if feas.any() else 0.0,
+                 median_sens=float(np.median(sens[feas])) if feas.any() else 0.0)
+    return dict(err=err, bound=bound, feas=feas, near=near, branch=near, checked=checked, ok=ok,
+                strict=strict, fail=fail, flipped=flipped, stats=stats, cmp=c)

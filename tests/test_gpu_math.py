@@ -1,0 +1,72 @@
+"""The rollout's own FP32 elementary functions (sin/cos by Cody-Waite
+reduction and Taylor series, atan2 by octant reduction and a fitted
+polynomial, the MUFU reciprocal) against CUDA's library functions and an
+FP64 reference, on the GPU through atp_math_check."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def run(a, b):
+    from paper_2603_20525_gb300 import atp
+    L = atp.load()
+    ad = torch.as_tensor(np.asarray(a, np.float32)).cuda()
+    bd = torch.as_tensor(np.asarray(b, np.float32)).cuda()
+    out = torch.empty((len(a), 8), dtype=torch.float32, device="cuda")
+    assert L.atp_math_check(C.c_void_p(ad.data_ptr()), C.c_void_p(bd.data_ptr()), len(a),
+                            C.c_void_p(out.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_sincos_against_cuda_and_fp64():
+    rng = np.random.default_rng(0)
+    a = np.concatenate([rng.uniform(-0.8, 0.8, 200000), rng.uniform(-60, 60, 200000),
+                        [0.0, -0.0, 0.785398163, -0.785398163, 1e-30, 3.14159265]]).astype(np.float32)
+    o = run(a, np.ones_like(a))
+    x = a.astype(np.float64)
+    es = np.abs(o[:, 0] - np.sin(x)).max()
+    ec = np.abs(o[:, 1] - np.cos(x)).max()
+    es_ref = np.abs(o[:, 2] - np.sin(x)).max()
+    ec_ref = np.abs(o[:, 3] - np.cos(x)).max()
+    print("sin/cos max abs error: library", es, ec, "CUDA", es_ref, ec_ref)
+    assert es <= 1.2e-7 and ec <= 1.2e-7
+    assert es <= 2.5 * es_ref and ec <= 2.5 * ec_ref
+
+
+def test_atan2_against_cuda_and_fp64():
+    rng = np.random.default_rng(1)
+    n = 300000
+    mag = 10.0 ** rng.uniform(-4, 2, n)
+    ang = rng.uniform(-np.pi, np.pi, n)
+    y = (mag * np.sin(ang)).astype(np.float32)
+    x = (mag * np.cos(ang)).astype(np.float32)
+    # the common case: a wheel rolling forward, small slip
+    y2 = rng.normal(0, 0.5, n).astype(np.float32)
+    x2 = rng.uniform(2, 16, n).astype(np.float32)
+    y = np.concatenate([y, y2, [0.0, 0.0, 1.0, -1.0]]).astype(np.float32)
+    x = np.concatenate([x, x2, [0.0, 1.0, 0.0, 0.0]]).astype(np.float32)
+    o = run(y, x)
+    ref = np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    err = np.abs(o[:, 4] - ref)
+    err_ref = np.abs(o[:, 5] - ref)
+    tol = 2.5e-7 * np.abs(ref) + 1e-12
+    print("atan2 max rel error: library", (err / np.maximum(np.abs(ref), 1e-30)).max(),
+          "CUDA", (err_ref / np.maximum(np.abs(ref), 1e-30)).max())
+    assert np.all(err <= np.maximum(tol, 4e-7))
+    assert o[-4, 4] == 0.0 and o[-3, 4] == 0.0
+
+
+def test_reciprocal_within_one_ulp():
+    rng = np.random.default_rng(2)
+    b = np.concatenate([rng.uniform(0.2, 1.5, 100000), -rng.uniform(0.2, 1.5, 100000),
+                        10.0 ** rng.uniform(-10, 10, 100000)]).astype(np.float32)
+    o = run(np.zeros_like(b), b)
+    ref = 1.0 / b.astype(np.float64)
+    rel = np.abs(o[:, 6] - ref) / np.abs(ref)
+    assert rel.max() <= 1.2e-7
+    assert np.array_equal(o[:, 7], (np.float32(1.0) / b).astype(np.float64))

@@ -64,15 +64,16 @@ def check_plan(g, o, w, ctrl=None, x0=None):
     sens = parity.conditioning(oracle, w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, o)
     v = parity.classify(g, o, sens, w.vehicle)
     print("parity", w.name, v["stats"])
-    # every feasible candidate away from a discontinuity agrees within
-    # max(1e-4, KAPPA x its own FP64 conditioning)
-    bad = np.nonzero(v["checked"] & ~v["ok"])[0]
+    # every feasible candidate agrees within max(1e-4, KAPPA x its own FP64
+    # conditioning), except at most 1 % that took the other side of a switch
+    bad = np.nonzero(v["fail"])[0]
     assert bad.size == 0, [(int(j), float(v["err"][j]), float(v["bound"][j])) for j in bad[:5]]
-    # all flag bits agree on those candidates; the feasibility bit agrees on
-    # every candidate that does not pass near U_ESM = 0 or a touchdown
+    assert v["stats"]["switch_misses"] <= max(1, 0.01 * v["stats"]["feasible"])
+    # all flag bits agree on the candidates that held the bound; the
+    # feasibility bit agrees on every candidate away from a switch
     ck = v["checked"]
     assert np.array_equal(g["flags"][ck], o["flags"][ck])
-    sure = ~v["branch"]
+    sure = ~v["near"]
     assert np.array_equal(g["flags"][sure] & 1, o["flags"][sure] & 1)
     # reduction: bit-exact over the GPU's own per-candidate outputs
     assert g["best_idx"] == lexmin(g["cost"], g["flags"])
@@ -117,7 +118,7 @@ def test_plain_plan_parity(ctx):
     g = gpu_plan(ctx, w)
     o = oracle_plan(w)
     s = check_plan(g, o, w)
-    assert s["checked"] >= 0.9 * s["feasible"] and s["strict_frac"] >= 0.6
+    assert s["strict_frac"] >= 0.6
 
 
 @pytest.mark.parametrize("seed", [1, 2])
@@ -132,7 +133,7 @@ def test_scaled_plan_parity(ctx):
     g = gpu_plan(ctx, w)
     o = oracle_plan(w)
     s = check_plan(g, o, w)
-    assert s["checked"] >= 0.9 * s["feasible"] and s["strict_frac"] >= 0.5
+    assert s["strict_frac"] >= 0.5
 
 
 def test_rollout_equals_plan_outputs(ctx):
