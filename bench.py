@@ -203,6 +203,33 @@ def cpu_baseline(w, budget_s=10.0):
             "sample": f"{n} whole plans of the workload ({n * w.N} candidates, {el:.1f} s), FP64"}
 
 
+def run_serving(seconds, device):
+    """The serving stream: 32 vehicles, each on its own resident 512-2048^2
+    tile, Poisson plan requests at 20 Hz per vehicle with N in {1k, 4k, 16k,
+    32k}, H uniform in [40, 150], dt in {0.020, 0.025, ..., 0.050} s, warm
+    started from the vehicle's previous plan; continuous batching against the
+    plain single-plan path replaying the same trace one request at a time."""
+    import gen
+    from paper_2603_20525_gb300 import serve
+    fl = gen.fleet(32, seed=0)
+    vehicles = serve.resident_vehicles(fl, device=device)
+    srv = serve.Server(vehicles, streams=2, slot_candidates=1 << 17, arena_bytes=2 << 30,
+                       device=device)
+    srv.serve(serve.poisson_trace(32, 20.0, 0.5, seed=99))          # warm-up
+    serve.reset_warm_start(vehicles)
+    trace = serve.poisson_trace(32, 20.0, seconds, seed=1)
+    served = srv.serve(trace)
+    serve.reset_warm_start(vehicles)
+    plain = srv.sequential(trace)
+    same = all(a.best_idx == b.best_idx and a.best_cost == b.best_cost for a, b in zip(served, plain))
+    return {"workload": "32 vehicles x 20 Hz Poisson, N in {1024, 4096, 16384, 32768}, "
+                        "H 40-150, dt 0.02-0.05 s, own 512-2048^2 tile at 0.1 m, warm start",
+            "trace_s": seconds, "requests": len(trace),
+            "served": serve.latency_summary(served),
+            "plain_sequential": serve.latency_summary(plain),
+            "identical_results": bool(same)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +238,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scaled", choices=["scaled", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=6.0,
+                    help="seconds of the 32-vehicle request stream (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -332,6 +361,8 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
         }
+        if args.serve_seconds > 0:
+            line["serving"] = run_serving(args.serve_seconds, local)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

@@ -137,15 +137,23 @@ def fbm(n: int, cell: float, amplitude: float, seed: int, stream: int = 1,
     ang = 2.0 * math.pi * u[: octaves * dirs]
     phs = 2.0 * math.pi * u[octaves * dirs:]
     c = cell * np.arange(n, dtype=np.float64)
-    X, Y = np.meshgrid(c, c)
-    f = np.zeros((n, n))
+    # cos(kx x + ky y + p) = cos(kx x) cos(ky y + p) - sin(kx x) sin(ky y + p):
+    # every wave is a rank-2 outer product, so the sum is one matrix product
+    A = np.empty((n, 2 * octaves * dirs))
+    B = np.empty((2 * octaves * dirs, n))
     for o in range(octaves):
         lam = lambda0 / 2.0 ** o
         g = 0.5 ** o
         for d in range(dirs):
-            a = ang[o * dirs + d]
-            p = phs[o * dirs + d]
-            f += g * np.cos((2.0 * math.pi / lam) * (X * math.cos(a) + Y * math.sin(a)) + p)
+            w = o * dirs + d
+            a, p = ang[w], phs[w]
+            kx = (2.0 * math.pi / lam) * math.cos(a)
+            ky = (2.0 * math.pi / lam) * math.sin(a)
+            A[:, 2 * w] = g * np.cos(ky * c + p)
+            A[:, 2 * w + 1] = -g * np.sin(ky * c + p)
+            B[2 * w] = np.cos(kx * c)
+            B[2 * w + 1] = np.sin(kx * c)
+    f = A @ B
     return f * (amplitude / np.max(np.abs(f)))
 
 
@@ -348,3 +356,33 @@ def workload_scaled(seed: int = 0, N: int = 16384, H: int = 100, dt: float = 0.0
 def n_substeps(dt: float, h_max: float = 0.005) -> int:
     """Euler substeps per control step: ceil(dt / 5 ms)."""
     return max(1, math.ceil(round(dt / h_max, 9)))
+
+
+@dataclass
+class FleetVehicle:
+    """One vehicle of a serving fleet: its own terrain tile, parameters,
+    goal and settled start."""
+    terrain: Terrain
+    vehicle: dict
+    cost: dict
+    x0: np.ndarray
+    key: tuple
+
+
+def fleet(n: int = 32, seed: int = 0, sides=(512, 1024, 2048)):
+    """n vehicles, each on its own seeded 0.1 m tile of side drawn from
+    `sides`, alternately the benchmark vehicle and the MRZR, started settled
+    at the tile centre at 5-10 m/s with the goal 40 m ahead."""
+    u = uniform(seed, 41, 4 * n)
+    out = []
+    for v in range(n):
+        side = int(sides[min(int(u[4 * v] * len(sides)), len(sides) - 1)])
+        t = terrain_tile(side, seed * 1000 + v)
+        veh = vehicle_baseline() if v % 2 == 0 else vehicle_mrzr()
+        ext = side * t.cell
+        psi = math.pi * (2.0 * u[4 * v + 1] - 1.0)
+        x = y = 0.5 * ext
+        x0 = settled_state(t, veh, x, y, psi, 5.0 + 5.0 * u[4 * v + 2])
+        cost = cost_default(x + 40.0 * math.cos(psi), y + 40.0 * math.sin(psi))
+        out.append(FleetVehicle(t, veh, cost, x0, (seed + 1, v + 1)))
+    return out

@@ -138,9 +138,10 @@ int atp_destroy(atp_ctx *ctx);
 /* One-line description of the last error on this context ("" if none). */
 const char *atp_last_error(const atp_ctx *ctx);
 
-/* Pre-size the context scratch for plans of up to N candidates and H control
- * steps, so that later calls allocate nothing.  Without it, atp_plan grows the
- * scratch on first use of a larger size (a synchronous cudaMalloc). */
+/* Pre-size the context scratch for plans (or batches, see atp_plan_batch) of
+ * up to N candidates in total and H control steps, so that later calls
+ * allocate nothing.  Without it, a call grows the scratch on first use of a
+ * larger size (a synchronous cudaMalloc after a device synchronize). */
 int atp_reserve(atp_ctx *ctx, int N, int H);
 
 /* Bytes of device memory a prepared terrain of nx x ny nodes needs. */
@@ -191,6 +192,48 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
                 const float *ctrl_dev, int N, int H, float dt, int n_sub,
                 float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
                 float *cand_xf_dev, float *step_margin_dev, void *stream);
+
+/* One plan of a batch: the arguments of atp_plan gathered in a struct.  The
+ * struct pointers (veh, cost, terrain, x0) are host memory read during the
+ * call; the *_dev pointers are device memory as for atp_plan. */
+typedef struct {
+    const atp_vehicle *veh;
+    const atp_cost *cost;
+    const atp_terrain *terrain;
+    const atp_state *x0;
+    const float *x0_dev;
+    const float *ctrl_dev;
+    int N, H;
+    float dt;
+    int n_sub;
+    atp_plan_out *out_dev;
+    float *best_ctrl_dev, *best_margin_dev;
+    float *cand_cost_dev, *cand_margin_dev;
+    uint8_t *cand_flags_dev;
+    float *cand_xf_dev;
+} atp_plan_request;
+
+/* Continuous batching: n_req (1..64) independent plans, each with its own
+ * vehicle, terrain, candidates, horizon and outputs, in one kernel launch.
+ * Each plan's results are bit-identical to a single atp_plan of the same
+ * request for N <= 131072 (both run four lanes per candidate), alone or in
+ * any mix.  The context's scratch grows to the sum of the plans' needs;
+ * atp_reserve(ctx, sum of N, max H) pre-sizes it for any batch within those
+ * totals.  Validation failures name the offending request in atp_last_error. */
+int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *stream);
+
+/* Candidate sampler (the on-GPU drawing of Sec. IV-D): writes float2
+ * ctrl[H][N] with ctrl[k][j] = nominal[k] + (sigma_rate n1, sigma_acc n2),
+ * where (n1, n2) is the Box-Muller pair of two 23-bit uniforms taken from the
+ * top bits of the first two words of Philox4x64-10 (Salmon et al., SC'11) at
+ * counter (j, k, nonce, 0) under key (key0, key1); candidate 0 is the nominal.
+ * The nominal is a warm start from the previous plan's best controls,
+ * nominal[k] = prev_best[min(k + shift, H_prev - 1)] (float [H_prev][2],
+ * device), or zero when H_prev = 0.  Draws depend only on (key, nonce, j, k),
+ * not on the launch.  1 <= H <= 65535. */
+int atp_sample(atp_ctx *ctx, const float *prev_best_dev, int H_prev, int shift, double sigma_rate,
+               double sigma_acc, uint64_t key0, uint64_t key1, uint64_t nonce, int N, int H,
+               float *ctrl_dev, void *stream);
 
 /* Diagnostic: evaluates the library's own FP32 elementary functions next to
  * CUDA's on n input pairs (a_i, b_i), writing 8 floats per pair to out_dev:

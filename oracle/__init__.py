@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  It is an
 independent restatement of the paper in plain C (``srb.c``), built with gcc
-into ``oracle/_build/liboracle.so`` and called through ctypes.  It shares no
+into ``oracle/_build/liboracle.so`` and called through ctypes; ``sampler.c``
+restates the candidate sampler (Philox4x64-10 and Box-Muller).  It shares no
 code with the CUDA path, and the product never falls back to it.
 """
 from __future__ import annotations
@@ -16,7 +17,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "srb.c")]
+_SRC = [os.path.join(_HERE, "srb.c"), os.path.join(_HERE, "sampler.c")]
 _HDR = [os.path.join(_HERE, "oracle.h")]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
@@ -93,6 +94,10 @@ def lib():
             L.orc_trajectory.restype = C.c_int
             L.orc_select.argtypes = [_dp, _up, C.c_int]
             L.orc_select.restype = C.c_int
+            _u64p = C.POINTER(C.c_uint64)
+            L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
+            L.orc_sample.argtypes = [_fp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
+                                     C.c_uint64, C.c_uint64, C.c_int, C.c_int, _dp]
             _lib = L
     return _lib
 
@@ -218,3 +223,25 @@ def trajectory(veh: dict, cst: dict, ter: Terrain, x0, ctrl_h2, dt: float, n_sub
                               _ptr(x0, _dp), _ptr(ctrl_h2, _fp), H, float(dt), int(n_sub),
                               _ptr(states, _dp), _ptr(Jrun, _dp))
     return states, Jrun, int(ds)
+
+
+def philox4x64_10(ctr, key):
+    """The four 64-bit Philox words at counter `ctr` (4 ints) under `key` (2)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.empty(4, dtype=np.uint64)
+    p = C.POINTER(C.c_uint64)
+    lib().orc_philox4x64_10(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
+
+
+def sample(prev, shift, sigma_rate, sigma_acc, key, nonce, N, H):
+    """Warm-started Gaussian candidates, FP64 [H, N, 2] (see sampler.c)."""
+    if prev is None:
+        prev = np.zeros((0, 2), np.float32)
+    prev = np.ascontiguousarray(prev, dtype=np.float32)
+    out = np.empty((H, N, 2))
+    lib().orc_sample(_ptr(prev, _fp), int(prev.shape[0]), int(shift), float(sigma_rate),
+                     float(sigma_acc), int(key[0]), int(key[1]), int(nonce), int(N), int(H),
+                     _ptr(out, _dp))
+    return out

@@ -25,7 +25,7 @@ FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
 # every symbol include/atp.h declares
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
-           "atp_plan_noalloc", "atp_math_check")
+           "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch")
 
 
 class Vehicle(C.Structure):
@@ -48,6 +48,16 @@ class TerrainC(C.Structure):
     _fields_ = [("texels", C.c_void_p), ("nx", C.c_int), ("ny", C.c_int),
                 ("cell", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
                 ("format", C.c_int)]
+
+
+class PlanRequest(C.Structure):
+    _fields_ = [("veh", C.POINTER(Vehicle)), ("cost", C.POINTER(Cost)),
+                ("terrain", C.POINTER(TerrainC)), ("x0", C.POINTER(State)),
+                ("x0_dev", C.c_void_p), ("ctrl_dev", C.c_void_p), ("N", C.c_int), ("H", C.c_int),
+                ("dt", C.c_float), ("n_sub", C.c_int), ("out_dev", C.c_void_p),
+                ("best_ctrl_dev", C.c_void_p), ("best_margin_dev", C.c_void_p),
+                ("cand_cost_dev", C.c_void_p), ("cand_margin_dev", C.c_void_p),
+                ("cand_flags_dev", C.c_void_p), ("cand_xf_dev", C.c_void_p)]
 
 
 class PlanOut(C.Structure):
@@ -93,8 +103,12 @@ def load(build_if_missing: bool = True):
                                        C.POINTER(State), _vp, _vp, C.c_int, C.c_int, C.c_float,
                                        C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.atp_math_check.argtypes = [_vp, _vp, C.c_int, _vp, _vp]
+        L.atp_plan_batch.argtypes = [_vp, C.POINTER(PlanRequest), C.c_int, _vp]
+        L.atp_sample.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
+                                 C.c_uint64, C.c_uint64, C.c_int, C.c_int, _vp, _vp]
         for n in ("atp_create", "atp_destroy", "atp_reserve", "atp_terrain_prepare",
-                  "atp_plan", "atp_rollout", "atp_plan_noalloc", "atp_math_check"):
+                  "atp_plan", "atp_rollout", "atp_plan_noalloc", "atp_math_check", "atp_sample",
+                  "atp_plan_batch"):
             getattr(L, n).restype = C.c_int
         _lib = L
         return L
@@ -206,6 +220,46 @@ class Context:
         self._check(rc, "atp_plan")
         return o
 
+    def plan_batch(self, requests, stream=None):
+        """One launch over a ragged batch of plans.  Each request is a dict
+        with veh, cost, terrain (Terrain), x0 (13 floats or CUDA [13, N]),
+        ctrl (CUDA [H, N, 2]), dt, n_sub and an `out` dict of output tensors
+        as returned by plan_outputs()."""
+        import torch
+        n = len(requests)
+        arr = (PlanRequest * n)()
+        keep = []
+        for i, q in enumerate(requests):
+            H, N, _ = q["ctrl"].shape
+            veh, cst = vehicle(q["veh"]), cost(q["cost"])
+            x0 = q["x0"]
+            xs, xdev = (None, x0) if isinstance(x0, torch.Tensor) else (state(x0), None)
+            keep += [veh, cst, xs]
+            o = q["out"]
+            arr[i] = PlanRequest(C.pointer(veh), C.pointer(cst), C.pointer(q["terrain"].c),
+                                 C.pointer(xs) if xs is not None else None,
+                                 None if xdev is None else xdev.data_ptr(), q["ctrl"].data_ptr(),
+                                 int(N), int(H), float(q["dt"]), int(q.get("n_sub", 0)),
+                                 o["out"].data_ptr(),
+                                 *[None if o.get(k) is None else o[k].data_ptr()
+                                   for k in ("best_ctrl", "best_margin", "cost", "margin",
+                                             "flags", "xf")])
+        rc = self.lib.atp_plan_batch(self.h, arr, n, _stream(stream))
+        self._check(rc, "atp_plan_batch")
+        return [q["out"] for q in requests]
+
+    def sample(self, N, H, sigma_rate, sigma_acc, key, nonce, prev=None, shift=1, out=None,
+               stream=None):
+        """Warm-started Gaussian candidates float32 CUDA [H, N, 2] (atp_sample)."""
+        import torch
+        ctrl = out if out is not None else torch.empty((H, N, 2), dtype=torch.float32, device="cuda")
+        Hp = 0 if prev is None else int(prev.shape[0])
+        rc = self.lib.atp_sample(self.h, _ptr(prev), Hp, int(shift), float(sigma_rate),
+                                 float(sigma_acc), int(key[0]), int(key[1]), int(nonce), int(N),
+                                 int(H), _ptr(ctrl), _stream(stream))
+        self._check(rc, "atp_sample")
+        return ctrl
+
     def rollout(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0,
                 want_xf=True, want_step_margin=False, stream=None):
         import torch
@@ -226,6 +280,21 @@ class Context:
                                   _ptr(o.get("xf")), _ptr(o.get("step_margin")), _stream(stream))
         self._check(rc, "atp_rollout")
         return o
+
+
+def plan_outputs(N, H, device="cuda", candidates=True, xf=False):
+    """Output tensors of one plan (for Context.plan(out=...) and plan_batch)."""
+    import torch
+    o = dict(out=torch.zeros(6, dtype=torch.int32, device=device),
+             best_ctrl=torch.empty((H, 2), dtype=torch.float32, device=device),
+             best_margin=torch.empty(H, dtype=torch.float32, device=device))
+    if candidates:
+        o["cost"] = torch.empty(N, dtype=torch.float32, device=device)
+        o["margin"] = torch.empty(N, dtype=torch.float32, device=device)
+        o["flags"] = torch.empty(N, dtype=torch.uint8, device=device)
+    if xf:
+        o["xf"] = torch.empty((13, N), dtype=torch.float32, device=device)
+    return o
 
 
 def decode_out(t) -> dict:

@@ -40,13 +40,24 @@ def _inputs():
 
 
 def flags():
-    return [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # -fmad=false: no implicit FMA contraction; the kernels write every fused
+    # multiply-add as fmaf, so results do not depend on how a function was
+    # inlined (single plans and batches give the same bits)
+    return [ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
             f"-I{INCLUDE}", f"-I{CSRC}"]
+
+
+STAMP = os.path.join(LIBDIR, "flags.txt")
+
+
+def _stamp() -> str:
+    return " ".join(flags()) + "\n"
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(p) for p in _inputs())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+    same_flags = os.path.exists(STAMP) and open(STAMP).read() == _stamp()
+    if not force and same_flags and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     objdir = os.path.join(LIBDIR, "obj")
     os.makedirs(objdir, exist_ok=True)
@@ -73,6 +84,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(_stamp())
     for o in objs:
         os.remove(o)
     return LIB

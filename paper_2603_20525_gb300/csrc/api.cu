@@ -11,13 +11,14 @@
 
 #include "atp.h"
 #include "plan_kernel.cuh"
+#include "sampler.cuh"
 
 struct atp_ctx {
     int device;
     char err[256];
-    void *scratch;            // atp::Scratch + per-candidate buffers
+    void *scratch;            // reduction headers + per-plan candidate buffers
     size_t scratch_bytes;
-    int capN, capH;
+    atp::BatchParams *batch;  // host staging of one batch's descriptors
 };
 
 namespace {
@@ -76,33 +77,56 @@ ScratchLayout layout(size_t N, size_t H)
     return L;
 }
 
-int ensure_scratch(atp_ctx *ctx, int N, int H)
+// Context scratch: kMaxBatch reduction headers at fixed offsets (each plan's
+// last CTA restores its header, so they stay valid across calls), then one
+// region per plan of the call.
+constexpr size_t kHeaderBytes = (atp::kMaxBatch * sizeof(atp::Scratch) + kAlign - 1) / kAlign * kAlign;
+
+struct RegionLayout {
+    size_t cost, margin, flags, step_margin, total;
+};
+
+RegionLayout region_layout(size_t N, size_t H)
 {
-    if (ctx->scratch && N <= ctx->capN && H <= ctx->capH) return ATP_OK;
-    const int nN = N > ctx->capN ? N : ctx->capN;
-    const int nH = H > ctx->capH ? H : ctx->capH;
-    const ScratchLayout L = layout((size_t)nN, (size_t)nH);
+    RegionLayout L;
+    size_t o = 0;
+    L.cost = o;        o = align_up(o + N * sizeof(float));
+    L.margin = o;      o = align_up(o + N * sizeof(float));
+    L.flags = o;       o = align_up(o + N);
+    L.step_margin = o; o = align_up(o + N * H * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+int ensure_scratch_bytes(atp_ctx *ctx, size_t need)
+{
+    need += kHeaderBytes;
+    if (ctx->scratch && need <= ctx->scratch_bytes) return ATP_OK;
     if (ctx->scratch) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(ctx, e, "synchronize before growing scratch");
         cudaFree(ctx->scratch);
         ctx->scratch = nullptr;
-        ctx->capN = ctx->capH = 0;
+        ctx->scratch_bytes = 0;
     }
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, L.total);
+    cudaError_t e = cudaMalloc(&p, need);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
-    atp::Scratch init{~0ull, 0u, 0u};
-    e = cudaMemcpy(p, &init, sizeof init, cudaMemcpyHostToDevice);
+    atp::Scratch init[atp::kMaxBatch];
+    for (auto &h : init) h = atp::Scratch{~0ull, 0u, 0u};
+    e = cudaMemcpy(p, init, sizeof init, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(p);
         return cuda_fail(ctx, e, "scratch initialisation");
     }
     ctx->scratch = p;
-    ctx->scratch_bytes = L.total;
-    ctx->capN = nN;
-    ctx->capH = nH;
+    ctx->scratch_bytes = need;
     return ATP_OK;
+}
+
+int ensure_scratch(atp_ctx *ctx, int N, int H)
+{
+    return ensure_scratch_bytes(ctx, region_layout((size_t)N, (size_t)H).total);
 }
 
 int check_vehicle(atp_ctx *ctx, const atp_vehicle *v)
@@ -232,7 +256,9 @@ int common_checks(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, co
     if (!(dt > 0.f) || !std::isfinite(dt)) return fail(ctx, ATP_ERR_INVALID, "dt must be finite and > 0");
     if (n_sub < 0 || n_sub > 1000000) return fail(ctx, ATP_ERR_INVALID, "n_sub must be in [0, 1e6]");
     if (n_sub == 0) {
-        double q = std::ceil((double)dt / 0.005 - 1e-9);
+        // ceil(dt / 5 ms), with a dt within FP32 rounding of a multiple of
+        // 5 ms taken as that multiple (0.025f is 0.0250000004)
+        double q = std::ceil((double)dt / 0.005 - 1e-5);
         n_sub = q < 1.0 ? 1 : (int)q;
     }
     *n_sub_out = n_sub;
@@ -272,13 +298,20 @@ int atp_create(atp_ctx **out, int device)
     if (!ctx) return ATP_ERR_NOMEM;
     ctx->device = device;
     ctx->err[0] = 0;
+    ctx->batch = new (std::nothrow) atp::BatchParams;
+    if (!ctx->batch) {
+        delete ctx;
+        return ATP_ERR_NOMEM;
+    }
     DeviceGuard g(device);
     if (g.err != cudaSuccess) {
+        delete ctx->batch;
         delete ctx;
         return ATP_ERR_CUDA;
     }
     int rc = ensure_scratch(ctx, 1, 1);
     if (rc != ATP_OK) {
+        delete ctx->batch;
         delete ctx;
         return rc;
     }
@@ -292,6 +325,7 @@ int atp_destroy(atp_ctx *ctx)
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->scratch) cudaFree(ctx->scratch);
+    delete ctx->batch;
     delete ctx;
     return ATP_OK;
 }
@@ -304,7 +338,10 @@ int atp_reserve(atp_ctx *ctx, int N, int H)
     if (N < 1 || H < 1) return fail(ctx, ATP_ERR_INVALID, "reserve needs N, H >= 1");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
-    return ensure_scratch(ctx, N, H);
+    // room for any batch of up to kMaxBatch plans within these totals: each
+    // plan's four arrays round up to kAlign at most once
+    return ensure_scratch_bytes(ctx, region_layout((size_t)N, (size_t)H).total +
+                                         (size_t)atp::kMaxBatch * 4 * kAlign);
 }
 
 size_t atp_terrain_bytes(int nx, int ny, int format)
@@ -359,8 +396,8 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
     if ((rc = ensure_scratch(ctx, N, H)) != ATP_OK) return rc;
-    const ScratchLayout L = layout((size_t)ctx->capN, (size_t)ctx->capH);
-    char *base = (char *)ctx->scratch;
+    const RegionLayout L = region_layout((size_t)N, (size_t)H);
+    char *base = (char *)ctx->scratch + kHeaderBytes;
     atp::PlanParams p;
     std::memset(&p, 0, sizeof p);
     derive(*veh, *cost, *terrain, p);
@@ -373,7 +410,7 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     p.out = out_dev;
     p.best_ctrl = best_ctrl_dev;
     p.best_margin = best_margin_dev;
-    p.scratch = (atp::Scratch *)base;
+    p.scratch = (atp::Scratch *)ctx->scratch;
     cudaError_t e = atp::launch_plan(p, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
     return ATP_OK;
@@ -405,6 +442,93 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
 }
 
 }  // extern "C"
+
+extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (!reqs || n_req < 1 || n_req > atp::kMaxBatch)
+        return fail(ctx, ATP_ERR_INVALID, "need 1 <= n_req <= %d requests", atp::kMaxBatch);
+    size_t need = 0;
+    long long ctas = 0;
+    int ns[atp::kMaxBatch];
+    for (int r = 0; r < n_req; ++r) {
+        const atp_plan_request &q = reqs[r];
+        int rc = common_checks(ctx, q.veh, q.cost, q.terrain, q.x0, q.x0_dev, q.ctrl_dev, q.N, q.H,
+                               q.dt, q.n_sub, &ns[r]);
+        if (rc != ATP_OK) {
+            char why[sizeof ctx->err];
+            std::memcpy(why, ctx->err, sizeof why);
+            return fail(ctx, rc, "request %d: %s", r, why);
+        }
+        if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
+        if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
+        need += region_layout((size_t)q.N, (size_t)q.H).total;
+        ctas += ((long long)q.N * 4 + atp::kPlanBlock - 1) / atp::kPlanBlock;
+    }
+    if (ctas > 0x7fffffffLL) return fail(ctx, ATP_ERR_UNSUPPORTED, "batch too large");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    int rc = ensure_scratch_bytes(ctx, need);
+    if (rc != ATP_OK) return rc;
+    atp::BatchParams &b = *ctx->batch;
+    b.n = n_req;
+    b.cta_begin[0] = 0;
+    char *region = (char *)ctx->scratch + kHeaderBytes;
+    for (int r = 0; r < n_req; ++r) {
+        const atp_plan_request &q = reqs[r];
+        const RegionLayout L = region_layout((size_t)q.N, (size_t)q.H);
+        atp::PlanParams &p = b.req[r];
+        std::memset(&p, 0, sizeof p);
+        derive(*q.veh, *q.cost, *q.terrain, p);
+        fill_problem(p, q.x0, q.x0_dev, q.ctrl_dev, q.N, q.H, q.dt, ns[r]);
+        p.cost = q.cand_cost_dev ? q.cand_cost_dev : (float *)(region + L.cost);
+        p.margin = q.cand_margin_dev ? q.cand_margin_dev : (float *)(region + L.margin);
+        p.flags = q.cand_flags_dev ? q.cand_flags_dev : (uint8_t *)(region + L.flags);
+        p.xf = q.cand_xf_dev;
+        p.step_margin = (float *)(region + L.step_margin);
+        p.out = q.out_dev;
+        p.best_ctrl = q.best_ctrl_dev;
+        p.best_margin = q.best_margin_dev;
+        p.scratch = (atp::Scratch *)ctx->scratch + r;
+        region += L.total;
+        b.cta_begin[r + 1] = b.cta_begin[r] + (q.N * 4 + atp::kPlanBlock - 1) / atp::kPlanBlock;
+    }
+    cudaError_t e = atp::launch_plan_batch(b, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch launch");
+    return ATP_OK;
+}
+
+extern "C" int atp_sample(atp_ctx *ctx, const float *prev_best_dev, int H_prev, int shift,
+                          double sigma_rate, double sigma_acc, uint64_t key0, uint64_t key1,
+                          uint64_t nonce, int N, int H, float *ctrl_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (!ctrl_dev || (uintptr_t)ctrl_dev % 8 != 0)
+        return fail(ctx, ATP_ERR_INVALID, "ctrl_dev must be non-NULL and 8-byte aligned");
+    if (N < 1 || H < 1 || H > 65535) return fail(ctx, ATP_ERR_INVALID, "need N >= 1 and 1 <= H <= 65535");
+    if (H_prev < 0 || shift < 0) return fail(ctx, ATP_ERR_INVALID, "H_prev and shift must be >= 0");
+    if (H_prev > 0 && (!prev_best_dev || (uintptr_t)prev_best_dev % 8 != 0))
+        return fail(ctx, ATP_ERR_INVALID, "prev_best_dev must be non-NULL and 8-byte aligned");
+    if (!(sigma_rate >= 0.0) || !(sigma_acc >= 0.0) || !std::isfinite(sigma_rate) || !std::isfinite(sigma_acc))
+        return fail(ctx, ATP_ERR_INVALID, "sigmas must be finite and >= 0");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    atp::SampleParams p;
+    p.prev = H_prev > 0 ? (const float2 *)prev_best_dev : nullptr;
+    p.H_prev = H_prev;
+    p.shift = shift;
+    p.sigma_rate = (float)sigma_rate;
+    p.sigma_acc = (float)sigma_acc;
+    p.key0 = key0;
+    p.key1 = key1;
+    p.nonce = nonce;
+    p.N = N;
+    p.H = H;
+    p.ctrl = (float2 *)ctrl_dev;
+    cudaError_t e = atp::launch_sample(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sample launch");
+    return ATP_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Plan without allocation.  Some callers cannot allocate device memory once

@@ -44,23 +44,14 @@ __device__ __forceinline__ float quad_sum(float v, unsigned mask)
 // and the body-level arithmetic is repeated bit-identically on all four, so
 // the quad never needs to exchange state, only the five force/moment sums
 // and the costmap sum (two shuffles each).
-template <int LANES, bool PER_X0, bool REDUCE>
-__global__ void __launch_bounds__(kPlanBlock)
-plan_kernel(const __grid_constant__ PlanParams p)
+template <int LANES, bool PER_X0>
+__device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, unsigned qmask,
+                                            float &J, float &margin, bool &feasible)
 {
     const Veh &V = p.V;
     const Cost &Cc = p.C;
     const Terrain &T = p.T;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = tid / LANES;
-    const int q = LANES == 1 ? 0 : (tid & (LANES - 1));
-    const bool live = j < p.N;
-    const unsigned qmask = LANES == 1 ? 0u : (0xfu << (threadIdx.x & 28));
-
-    float J = 0.f, margin = CUDART_INF_F;
-    bool feasible = false;
-
-    if (live) {
+    {
         // this lane's wheel (LANES = 4)
         const bool front = q < 2;
         const float wrx = front ? V.Lf : -V.Lr;
@@ -125,11 +116,11 @@ plan_kernel(const __grid_constant__ PlanParams p)
                 Body B;
                 float *R = B.R;
                 R[0] = cps * cth;
-                R[1] = cps * sph * sth - cph * sps;
-                R[2] = sph * sps + cph * cps * sth;
+                R[1] = fmaf(cps * sph, sth, -cph * sps);
+                R[2] = fmaf(cph * cps, sth, sph * sps);
                 R[3] = cth * sps;
-                R[4] = cph * cps + sph * sps * sth;
-                R[5] = cph * sps * sth - cps * sph;
+                R[4] = fmaf(sph * sps, sth, cph * cps);
+                R[5] = fmaf(cph * sps, sth, -cps * sph);
                 R[6] = -sth;
                 R[7] = cth * sph;
                 R[8] = cph * cth;
@@ -155,40 +146,40 @@ plan_kernel(const __grid_constant__ PlanParams p)
                     const float Fyr = rl.Fy + rr.Fy;
                     FyB = Fyf + Fyr;
                     FzB = (fl.Fz + fr.Fz) + (rl.Fz + rr.Fz);
-                    Mx = V.he * ((fl.Fz - fr.Fz) + (rl.Fz - rr.Fz)) + V.hR * FyB;
-                    My = V.Lr * (rl.Fz + rr.Fz) - V.Lf * (fl.Fz + fr.Fz);
-                    Mz = V.Lf * Fyf - V.Lr * Fyr;
+                    Mx = fmaf(V.hR, FyB, V.he * ((fl.Fz - fr.Fz) + (rl.Fz - rr.Fz)));
+                    My = fmaf(V.Lr, rl.Fz + rr.Fz, -V.Lf * (fl.Fz + fr.Fz));
+                    Mz = fmaf(V.Lf, Fyf, -V.Lr * Fyr);
                     csum = (fl.cost + fr.cost) + (rl.cost + rr.cost);
                 } else {
                     const WheelOut w = wheel(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, off);
                     const float fy = front ? w.Fy * cd : w.Fy;
                     FyB = quad_sum(fy, qmask);
                     FzB = quad_sum(w.Fz, qmask);
-                    Mx = quad_sum(wry * w.Fz, qmask) + V.hR * FyB;
+                    Mx = fmaf(V.hR, FyB, quad_sum(wry * w.Fz, qmask));
                     My = quad_sum(-wrx * w.Fz, qmask);
                     Mz = quad_sum(wrx * fy, qmask);
                     csum = quad_sum(w.cost, qmask);
                 }
-                const float Fx = V.halfM * (ax - gBx + wy * vz - wz * vy);
+                const float Fx = V.halfM * fmaf(-wz, vy, fmaf(wy, vz, ax - gBx));
                 My = fmaf(-V.hR, 2.f * Fx, My);
                 // running cost L = L_0 + L_soft (Sec. IV-C), left Riemann sum
-                const float soft = fmaxf(1.f - U * Cc.inv_eps, 0.f);
-                const float L = Cc.wt + Cc.wc * dd * dd + Cc.sigma * soft * soft + csum;
+                const float soft = fmaxf(fmaf(-U, Cc.inv_eps, 1.f), 0.f);
+                const float L = fmaf(Cc.sigma * soft, soft, fmaf(Cc.wc * dd, dd, Cc.wt)) + csum;
                 J = fmaf(h, L, J);
                 // state derivative A(xi) + B zeta (Sec. IV-A)
                 const float ic = rcp(cth);
-                const float wsc = sph * wy + cph * wz;
-                const float dx = R[0] * vx + R[1] * vy + R[2] * vz;
-                const float dy = R[3] * vx + R[4] * vy + R[5] * vz;
-                const float dz = R[6] * vx + R[7] * vy + R[8] * vz;
+                const float wsc = fmaf(sph, wy, cph * wz);
+                const float dx = fmaf(R[2], vz, fmaf(R[1], vy, R[0] * vx));
+                const float dy = fmaf(R[5], vz, fmaf(R[4], vy, R[3] * vx));
+                const float dz = fmaf(R[8], vz, fmaf(R[7], vy, R[6] * vx));
                 const float dpsi = wsc * ic;
-                const float dth = cph * wy - sph * wz;
-                const float dph = wx + wsc * (sth * ic);
-                const float dvy = FyB * V.invM + gBy + wx * vz - wz * vx;
-                const float dvz = FzB * V.invM + gBz - wx * vy + wy * vx;
-                const float dwx = (Mx + V.dJyz * wy * wz) * V.invJxx;
-                const float dwy = (My - V.dJxz * wx * wz) * V.invJyy;
-                const float dwz = (Mz + V.dJxy * wx * wy) * V.invJzz;
+                const float dth = fmaf(cph, wy, -sph * wz);
+                const float dph = fmaf(wsc, sth * ic, wx);
+                const float dvy = fmaf(-wz, vx, fmaf(wx, vz, fmaf(FyB, V.invM, gBy)));
+                const float dvz = fmaf(wy, vx, fmaf(-wx, vy, fmaf(FzB, V.invM, gBz)));
+                const float dwx = fmaf(V.dJyz * wy, wz, Mx) * V.invJxx;
+                const float dwy = fmaf(-V.dJxz * wx, wz, My) * V.invJyy;
+                const float dwz = fmaf(V.dJxy * wx, wy, Mz) * V.invJzz;
                 // forward Euler (Sec. IV-D), steering angle clamped (reading Q5)
                 acc2(x, xl, h * dx);
                 acc2(y, yl, h * dy);
@@ -250,13 +241,17 @@ plan_kernel(const __grid_constant__ PlanParams p)
         }
     }
 
-    if (!REDUCE) return;
+}
 
-    // ---- empirical argmin (Sec. IV-D, reading Q7): min of (infeasible, J, j)
+// Empirical argmin of one plan (Sec. IV-D, reading Q7): the lexicographic
+// minimum of (infeasible, J, j) over the plan's n_ctas CTAs, then the last of
+// them writes the result.
+__device__ __forceinline__ void plan_tail(const PlanParams &p, int j, bool leader, float J,
+                                          bool feasible, unsigned n_ctas)
+{
     __shared__ unsigned long long s_key[kPlanBlock / 32];
     __shared__ unsigned int s_cnt[kPlanBlock / 32];
     __shared__ bool s_last;
-    const bool leader = live && q == 0;
     unsigned long long key = ~0ull;
     if (leader)
         key = ((unsigned long long)(feasible ? 0u : 1u) << 63) |
@@ -285,7 +280,7 @@ plan_kernel(const __grid_constant__ PlanParams p)
         atomicAdd(&p.scratch->count, bc);
         __threadfence();
         const unsigned int t = atomicAdd(&p.scratch->ticket, 1u);
-        s_last = (t == gridDim.x - 1);
+        s_last = (t == n_ctas - 1);
     }
     __syncthreads();
     if (!s_last) return;
@@ -305,7 +300,7 @@ plan_kernel(const __grid_constant__ PlanParams p)
     for (int k = threadIdx.x; k < p.H; k += blockDim.x) {
         const float2 u = __ldcg(p.ctrl + (size_t)k * N + best);
         if (p.best_ctrl) {
-            p.best_ctrl[2 * k] = clamp_keep_nan(u.x, -V.ddmax, V.ddmax);
+            p.best_ctrl[2 * k] = clamp_keep_nan(u.x, -p.V.ddmax, p.V.ddmax);
             p.best_ctrl[2 * k + 1] = u.y;
         }
         const float m = __ldcg(p.step_margin + (size_t)k * N + best);
@@ -330,6 +325,57 @@ plan_kernel(const __grid_constant__ PlanParams p)
         p.scratch->count = 0u;
         p.scratch->ticket = 0u;
     }
+}
+
+template <int LANES, bool PER_X0, bool REDUCE>
+__global__ void __launch_bounds__(kPlanBlock)
+plan_kernel(const __grid_constant__ PlanParams p)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = tid / LANES;
+    const int q = LANES == 1 ? 0 : (tid & (LANES - 1));
+    const bool live = j < p.N;
+    const unsigned qmask = LANES == 1 ? 0u : (0xfu << (threadIdx.x & 28));
+    float J = 0.f, margin = CUDART_INF_F;
+    bool feasible = false;
+    if (live) rollout_one<LANES, PER_X0>(p, j, q, qmask, J, margin, feasible);
+    if (!REDUCE) return;
+    plan_tail(p, j, live && q == 0, J, feasible, gridDim.x);
+}
+
+// Continuous batching: one launch over a ragged batch of plans, each with its
+// own vehicle, terrain, horizon, candidates and outputs.  Plan r owns CTAs
+// [cta_begin[r], cta_begin[r+1]) with four lanes per candidate; every
+// candidate runs exactly the code of a single plan, so its results are the
+// same bits alone and in any mix.
+__global__ void __launch_bounds__(kPlanBlock)
+plan_batch_kernel(const __grid_constant__ BatchParams b)
+{
+    int lo = 0, hi = b.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (b.cta_begin[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid;
+    }
+    const PlanParams &p = b.req[lo];
+    const int tid = ((int)blockIdx.x - b.cta_begin[lo]) * kPlanBlock + (int)threadIdx.x;
+    const int j = tid >> 2, q = tid & 3;
+    const bool live = j < p.N;
+    const unsigned qmask = 0xfu << (threadIdx.x & 28);
+    float J = 0.f, margin = CUDART_INF_F;
+    bool feasible = false;
+    if (live) {
+        if (p.x0_soa) rollout_one<4, true>(p, j, q, qmask, J, margin, feasible);
+        else rollout_one<4, false>(p, j, q, qmask, J, margin, feasible);
+    }
+    plan_tail(p, j, live && q == 0, J, feasible, (unsigned)(b.cta_begin[lo + 1] - b.cta_begin[lo]));
+}
+
+cudaError_t launch_plan_batch(const BatchParams &b, cudaStream_t stream)
+{
+    if (b.n < 1 || b.n > kMaxBatch) return cudaErrorInvalidValue;
+    plan_batch_kernel<<<(unsigned)b.cta_begin[b.n], kPlanBlock, 0, stream>>>(b);
+    return cudaGetLastError();
 }
 
 template <int LANES>

@@ -46,6 +46,18 @@ constexpr int kLanes4MaxN = 1 << 17;
 
 int plan_lanes(int N);
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream);
+
+// A ragged batch of plans in one launch.  The descriptors travel in the
+// kernel's parameter block (at most 32 KB), so a batch needs no device copy.
+constexpr int kMaxBatch = 64;
+struct BatchParams {
+    int n;
+    int cta_begin[kMaxBatch + 1];   // CTA prefix: plan r owns [cta_begin[r], cta_begin[r+1])
+    PlanParams req[kMaxBatch];
+};
+static_assert(sizeof(BatchParams) <= 32764, "batch descriptors exceed the kernel parameter limit");
+
+cudaError_t launch_plan_batch(const BatchParams &b, cudaStream_t stream);
 cudaError_t launch_terrain_prepare_f32(const float *heights, const float *costmap, int nx, int ny,
                                        float inv_cell, float4 *out, cudaStream_t stream);
 

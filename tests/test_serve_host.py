@@ -1,0 +1,72 @@
+"""Host-side logic of the serving loop (no GPU): the Poisson request trace,
+the device-arena allocator that admits requests by memory, and the buffer
+layout of one request."""
+import numpy as np
+import pytest
+
+from paper_2603_20525_gb300 import serve
+
+
+def test_trace_rates_and_ranges():
+    tr = serve.poisson_trace(n_vehicles=32, rate_hz=20.0, duration_s=30.0, seed=3)
+    assert all(tr[i].t_arrive <= tr[i + 1].t_arrive for i in range(len(tr) - 1))
+    per = np.bincount([r.vehicle for r in tr], minlength=32)
+    assert abs(per.mean() - 600) < 3 * np.sqrt(600 / 32)      # 20 Hz x 30 s per vehicle
+    assert {r.N for r in tr} == {1024, 4096, 16384, 32768}
+    assert min(r.H for r in tr) >= 40 and max(r.H for r in tr) <= 150
+    dts = {round(r.dt, 6) for r in tr}
+    assert dts <= {round(0.005 * k, 6) for k in range(4, 11)} and len(dts) == 7
+    gaps = np.diff([r.t_arrive for r in tr if r.vehicle == 0])
+    assert abs(gaps.mean() - 0.05) < 0.01                    # exponential, mean 50 ms
+
+
+class FakeArena(serve.DeviceArena):
+    """The allocator's bookkeeping without device memory."""
+
+    def __init__(self, nbytes):
+        self.nbytes = serve._align(nbytes)
+        self.free = [(0, self.nbytes)]
+        self.used = 0
+
+
+def test_arena_best_fit_coalesces_and_refuses():
+    a = FakeArena(10 * 256)
+    x = a.alloc(256 * 3)
+    y = a.alloc(256 * 2)
+    z = a.alloc(256 * 4)
+    assert a.alloc(256 * 2) is None                          # 1 block left
+    a.release(y, 256 * 2)
+    assert a.alloc(100) == 9 * 256                           # best fit: the 1-block hole
+    w = a.alloc(300)                                         # only the 2-block hole fits
+    assert w == y
+    a.release(9 * 256, 100)
+    a.release(x, 256 * 3)
+    a.release(w, 300)
+    a.release(z, 256 * 4)
+    assert a.free == [(0, 10 * 256)] and a.used == 0         # fully coalesced
+
+
+def test_arena_random_workload_never_overlaps():
+    rng = np.random.default_rng(1)
+    a = FakeArena(1 << 20)
+    live = {}
+    for _ in range(3000):
+        if live and rng.random() < 0.45:
+            off = list(live)[rng.integers(len(live))]
+            a.release(off, live.pop(off))
+        else:
+            n = int(rng.integers(1, 40000))
+            off = a.alloc(n)
+            if off is not None:
+                live[off] = n
+        spans = sorted((o, o + serve._align(n)) for o, n in live.items())
+        assert all(spans[i][1] <= spans[i + 1][0] for i in range(len(spans) - 1))
+        assert a.used == sum(serve._align(n) for n in live.values())
+        assert sum(s for _, s in a.free) + a.used == a.nbytes
+
+
+def test_request_layout_is_aligned_and_disjoint():
+    lay, total = serve.request_layout(16384, 100)
+    offs = [o for _, o, _, _ in lay]
+    assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
+    assert total >= 16384 * 100 * 8 + 16384 * 9 + 100 * 12 + 24
