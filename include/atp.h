@@ -66,7 +66,15 @@ enum {
 /* texel formats of a prepared terrain */
 enum {
     ATP_TERRAIN_F32X4 = 0,    /* float4 (f, f_x, f_y, cost) per node, 16 B */
-    ATP_TERRAIN_BF16X4 = 1    /* 4 x bf16 per node, 8 B */
+    ATP_TERRAIN_BF16X4 = 1    /* 4 x bf16 per node, 8 B: the height's and slopes'
+                                 residuals from their 8 x 8 block's FP32 plane (through
+                                 the block's first node, with its first row's and
+                                 column's slopes) and the cost; then the planes */
+};
+
+/* context options (atp_set_option) */
+enum {
+    ATP_OPT_COST_FP64 = 1     /* accumulate the running cost in FP64 (default 0: FP32) */
 };
 
 /* per-candidate flag bits */
@@ -144,8 +152,16 @@ const char *atp_last_error(const atp_ctx *ctx);
  * larger size (a synchronous cudaMalloc after a device synchronize). */
 int atp_reserve(atp_ctx *ctx, int N, int H);
 
-/* Bytes of device memory a prepared terrain of nx x ny nodes needs. */
+/* Bytes of device memory a prepared terrain of nx x ny nodes needs:
+ * 16 nx ny (F32X4); 8 nx ny rounded up to 256, plus 16 bytes per 8 x 8
+ * block (BF16X4). */
 size_t atp_terrain_bytes(int nx, int ny, int format);
+
+/* Set a context option for the calls that follow on this context:
+ * ATP_OPT_COST_FP64 (value 0 or 1) accumulates each candidate's running cost
+ * (time, control effort and the soft ESM and costmap constraints, Sec. IV-C)
+ * in FP64 instead of FP32.  Returns ATP_ERR_INVALID for an unknown option. */
+int atp_set_option(atp_ctx *ctx, int option, int value);
 
 /* Build the texels of a terrain: per node the height, its slope f_x, f_y by
  * central differences (one-sided on the border) and the optional costmap

@@ -118,13 +118,17 @@ class Terrain:
     """Oracle view of a heightmap: FP32 heights (the same bytes the GPU gets),
     FP64 node gradients computed here, optional FP32 costmap."""
 
-    def __init__(self, heights, cell, x0=0.0, y0=0.0, costmap=None):
+    def __init__(self, heights, cell, x0=0.0, y0=0.0, costmap=None, gx=None, gy=None):
         self.heights = np.ascontiguousarray(heights, dtype=np.float32)
         ny, nx = self.heights.shape
-        self.gx = np.empty((ny, nx), dtype=np.float64)
-        self.gy = np.empty((ny, nx), dtype=np.float64)
-        lib().orc_terrain_gradients(_ptr(self.heights, _fp), nx, ny, float(cell),
-                                    _ptr(self.gx, _dp), _ptr(self.gy, _dp))
+        if gx is None:
+            self.gx = np.empty((ny, nx), dtype=np.float64)
+            self.gy = np.empty((ny, nx), dtype=np.float64)
+            lib().orc_terrain_gradients(_ptr(self.heights, _fp), nx, ny, float(cell),
+                                        _ptr(self.gx, _dp), _ptr(self.gy, _dp))
+        else:                       # given node slopes (a stored terrain format)
+            self.gx = np.ascontiguousarray(gx, dtype=np.float64)
+            self.gy = np.ascontiguousarray(gy, dtype=np.float64)
         self.costmap = None if costmap is None else np.ascontiguousarray(costmap, np.float32)
         self.c = _Terrain(_ptr(self.heights, _fp), _ptr(self.gx, _dp), _ptr(self.gy, _dp),
                           _ptr(self.costmap, _fp), nx, ny, float(cell), float(x0), float(y0))
@@ -245,3 +249,55 @@ def sample(prev, shift, sigma_rate, sigma_acc, key, nonce, N, H):
                      float(sigma_acc), int(key[0]), int(key[1]), int(nonce), int(N), int(H),
                      _ptr(out, _dp))
     return out
+
+
+def bf16_round(x):
+    """float32 -> bf16 bits (uint16), round to nearest even."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return b.astype(np.uint16)
+
+
+def bf16_value(bits):
+    return (bits.astype(np.uint32) << 16).view(np.float32)
+
+
+def bf16_terrain(heights, cell):
+    """The BF16 terrain storage format restated on the host.  Per 8 x 8 block
+    the FP32 plane c0 + cx (i mod 8) + cy (j mod 8) through the block's first
+    node with the slopes of its first row and first column, every operation
+    rounded to FP32 on its own; per node the bf16 (round to nearest even) of
+    the height's residual from the plane and of the node slopes' (central
+    differences, one-sided on the border, in FP64, rounded to FP32) residuals
+    from the plane's slopes.  Returns
+    (decoded FP32 heights, decoded slopes gx, gy as FP64, the bf16 words
+    (res, gx, gy), the block planes [nby, nbx, 3])."""
+    f32 = np.float32
+    H = np.ascontiguousarray(heights, dtype=np.float32)
+    ny, nx = H.shape
+    nbx, nby = (nx + 7) // 8, (ny + 7) // 8
+    plane = np.zeros((nby, nbx, 3), np.float32)
+    for bj in range(nby):
+        for bi in range(nbx):
+            i0, j0 = 8 * bi, 8 * bj
+            ni, nj = min(8, nx - i0), min(8, ny - j0)
+            c0 = H[j0, i0]
+            cx = f32(f32(H[j0, i0 + ni - 1] - c0) * f32(f32(1.0) / f32(ni - 1))) if ni > 1 else f32(0)
+            cy = f32(f32(H[j0 + nj - 1, i0] - c0) * f32(f32(1.0) / f32(nj - 1))) if nj > 1 else f32(0)
+            plane[bj, bi] = (c0, cx, cy)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    P = plane[jj // 8, ii // 8]
+    base = (P[..., 0] + P[..., 1] * (ii & 7).astype(np.float32)).astype(np.float32)
+    base = (base + (P[..., 2] * (jj & 7).astype(np.float32)).astype(np.float32)).astype(np.float32)
+    res = (H - base).astype(np.float32)
+    g = Terrain(H, cell)
+    inv = np.float32(1.0 / cell)
+    px = (P[..., 1] * inv).astype(np.float32)          # the plane's slopes
+    py = (P[..., 2] * inv).astype(np.float32)
+    w_res = bf16_round(res)
+    w_gx = bf16_round((g.gx.astype(np.float32) - px).astype(np.float32))
+    w_gy = bf16_round((g.gy.astype(np.float32) - py).astype(np.float32))
+    h_dec = (base + bf16_value(w_res)).astype(np.float32)
+    gx_dec = (px + bf16_value(w_gx)).astype(np.float32)
+    gy_dec = (py + bf16_value(w_gy)).astype(np.float32)
+    return (h_dec, gx_dec.astype(np.float64), gy_dec.astype(np.float64), (w_res, w_gx, w_gy), plane)

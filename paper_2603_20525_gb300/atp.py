@@ -20,12 +20,14 @@ ATP_OK = 0
 ERRORS = {-1: "ATP_ERR_INVALID", -2: "ATP_ERR_UNSUPPORTED", -3: "ATP_ERR_NOMEM",
           -4: "ATP_ERR_CUDA", -5: "ATP_ERR_TIMEOUT"}
 F32X4, BF16X4 = 0, 1
+OPT_COST_FP64 = 1
 FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
 
 # every symbol include/atp.h declares
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
-           "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch")
+           "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch",
+           "atp_set_option")
 
 
 class Vehicle(C.Structure):
@@ -104,11 +106,12 @@ def load(build_if_missing: bool = True):
                                        C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.atp_math_check.argtypes = [_vp, _vp, C.c_int, _vp, _vp]
         L.atp_plan_batch.argtypes = [_vp, C.POINTER(PlanRequest), C.c_int, _vp]
+        L.atp_set_option.argtypes = [_vp, C.c_int, C.c_int]
         L.atp_sample.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_int, C.c_int, _vp, _vp]
         for n in ("atp_create", "atp_destroy", "atp_reserve", "atp_terrain_prepare",
                   "atp_plan", "atp_rollout", "atp_plan_noalloc", "atp_math_check", "atp_sample",
-                  "atp_plan_batch"):
+                  "atp_plan_batch", "atp_set_option"):
             getattr(L, n).restype = C.c_int
         _lib = L
         return L
@@ -175,6 +178,9 @@ class Context:
             msg = self.lib.atp_last_error(self.h).decode()
             raise AtpError(f"{what}: {ERRORS.get(rc, rc)}: {msg}")
 
+    def set_option(self, option: int, value: int):
+        self._check(self.lib.atp_set_option(self.h, int(option), int(value)), "atp_set_option")
+
     def reserve(self, N: int, H: int):
         self._check(self.lib.atp_reserve(self.h, int(N), int(H)), "atp_reserve")
 
@@ -183,7 +189,7 @@ class Context:
         import torch
         ny, nx = heights.shape
         nbytes = self.lib.atp_terrain_bytes(nx, ny, fmt)
-        tex = torch.empty(nbytes // 4, dtype=torch.float32, device=heights.device)
+        tex = torch.empty((nbytes + 3) // 4, dtype=torch.float32, device=heights.device)
         h = TerrainC()
         rc = self.lib.atp_terrain_prepare(self.h, _ptr(heights), _ptr(costmap), nx, ny,
                                           float(cell), float(x0), float(y0), int(fmt),

@@ -15,6 +15,7 @@
 
 struct atp_ctx {
     int device;
+    int acc64;                // ATP_OPT_COST_FP64
     char err[256];
     void *scratch;            // reduction headers + per-plan candidate buffers
     size_t scratch_bytes;
@@ -160,8 +161,8 @@ int check_cost(atp_ctx *ctx, const atp_cost *c)
 int check_terrain(atp_ctx *ctx, const atp_terrain *t)
 {
     if (!t || !t->texels) return fail(ctx, ATP_ERR_INVALID, "terrain or its texels is NULL");
-    if (t->format != ATP_TERRAIN_F32X4)
-        return fail(ctx, ATP_ERR_UNSUPPORTED, "terrain format %d not supported by this call", t->format);
+    if (t->format != ATP_TERRAIN_F32X4 && t->format != ATP_TERRAIN_BF16X4)
+        return fail(ctx, ATP_ERR_UNSUPPORTED, "terrain format %d not supported", t->format);
     if (t->nx < 3 || t->ny < 3 || t->nx > 65536 || t->ny > 65536)
         return fail(ctx, ATP_ERR_INVALID, "terrain must be between 3 and 65536 nodes per side");
     if (!(t->cell > 0.0) || !std::isfinite(t->cell) || !std::isfinite(t->x0) || !std::isfinite(t->y0))
@@ -227,7 +228,11 @@ void derive(const atp_vehicle &v, const atp_cost &c, const atp_terrain &t, atp::
     split(c.goal_y - t.y0, C.gy_hi, C.gy_lo);
     C.goal_r2 = (float)(c.goal_r * c.goal_r);
     atp::Terrain &T = p.T;
+    p.tex_format = t.format == ATP_TERRAIN_BF16X4 ? atp::TEX_BF16 : atp::TEX_F32;
     T.tex = (const float4 *)t.texels;
+    T.tex16 = (const uint2 *)t.texels;
+    T.plane16 = (const float4 *)((const char *)t.texels + atp::bf16_base_offset(t.nx, t.ny));
+    T.nbx = (t.nx + 7) / 8;
     T.nx = t.nx;
     T.ny = t.ny;
     T.inv_cell = (float)(1.0 / t.cell);
@@ -297,6 +302,7 @@ int atp_create(atp_ctx **out, int device)
     atp_ctx *ctx = new (std::nothrow) atp_ctx();
     if (!ctx) return ATP_ERR_NOMEM;
     ctx->device = device;
+    ctx->acc64 = 0;
     ctx->err[0] = 0;
     ctx->batch = new (std::nothrow) atp::BatchParams;
     if (!ctx->batch) {
@@ -347,8 +353,19 @@ int atp_reserve(atp_ctx *ctx, int N, int H)
 size_t atp_terrain_bytes(int nx, int ny, int format)
 {
     if (nx < 1 || ny < 1) return 0;
-    const size_t per = format == ATP_TERRAIN_BF16X4 ? 8 : 16;
-    return (size_t)nx * (size_t)ny * per;
+    if (format == ATP_TERRAIN_BF16X4)
+        return atp::bf16_base_offset(nx, ny) + (size_t)((nx + 7) / 8) * ((ny + 7) / 8) * 16;
+    return (size_t)nx * (size_t)ny * 16;
+}
+
+int atp_set_option(atp_ctx *ctx, int option, int value)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (option == ATP_OPT_COST_FP64) {
+        ctx->acc64 = value != 0;
+        return ATP_OK;
+    }
+    return fail(ctx, ATP_ERR_INVALID, "unknown option %d", option);
 }
 
 int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *costmap_dev, int nx,
@@ -361,14 +378,20 @@ int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *cos
         return fail(ctx, ATP_ERR_INVALID, "terrain must be between 3 and 65536 nodes per side");
     if (!(cell > 0.0) || !std::isfinite(cell) || !std::isfinite(x0) || !std::isfinite(y0))
         return fail(ctx, ATP_ERR_INVALID, "cell must be > 0 and origin finite");
-    if (format != ATP_TERRAIN_F32X4)
+    if (format != ATP_TERRAIN_F32X4 && format != ATP_TERRAIN_BF16X4)
         return fail(ctx, ATP_ERR_UNSUPPORTED, "terrain format %d not supported", format);
     if ((uintptr_t)texels_dev % 16 != 0) return fail(ctx, ATP_ERR_INVALID, "texels must be 16-byte aligned");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
-    cudaError_t e = atp::launch_terrain_prepare_f32(heights_dev, costmap_dev, nx, ny,
-                                                    (float)(1.0 / cell), (float4 *)texels_dev,
-                                                    (cudaStream_t)stream);
+    cudaError_t e;
+    if (format == ATP_TERRAIN_F32X4)
+        e = atp::launch_terrain_prepare_f32(heights_dev, costmap_dev, nx, ny, (float)(1.0 / cell),
+                                            (float4 *)texels_dev, (cudaStream_t)stream);
+    else
+        e = atp::launch_terrain_prepare_bf16(heights_dev, costmap_dev, nx, ny, (float)(1.0 / cell),
+                                             (uint2 *)texels_dev,
+                                             (float4 *)((char *)texels_dev + atp::bf16_base_offset(nx, ny)),
+                                             (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "terrain prepare launch");
     if (out) {
         out->texels = texels_dev;
@@ -411,6 +434,7 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     p.best_ctrl = best_ctrl_dev;
     p.best_margin = best_margin_dev;
     p.scratch = (atp::Scratch *)ctx->scratch;
+    p.acc64 = ctx->acc64;
     cudaError_t e = atp::launch_plan(p, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
     return ATP_OK;
@@ -436,6 +460,7 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
     p.flags = cand_flags_dev;
     p.xf = cand_xf_dev;
     p.step_margin = step_margin_dev;
+    p.acc64 = ctx->acc64;
     cudaError_t e = atp::launch_plan(p, false, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
     return ATP_OK;
@@ -490,6 +515,7 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         p.best_ctrl = q.best_ctrl_dev;
         p.best_margin = q.best_margin_dev;
         p.scratch = (atp::Scratch *)ctx->scratch + r;
+        p.acc64 = ctx->acc64;
         region += L.total;
         b.cta_begin[r + 1] = b.cta_begin[r] + (q.N * 4 + atp::kPlanBlock - 1) / atp::kPlanBlock;
     }

@@ -15,6 +15,7 @@
 //     CTA to write the result and the best candidate's controls and margins.
 #include "plan_kernel.cuh"
 
+#include <cuda_bf16.h>
 #include <math_constants.h>
 
 namespace atp {
@@ -44,7 +45,7 @@ __device__ __forceinline__ float quad_sum(float v, unsigned mask)
 // and the body-level arithmetic is repeated bit-identically on all four, so
 // the quad never needs to exchange state, only the five force/moment sums
 // and the costmap sum (two shuffles each).
-template <int LANES, bool PER_X0>
+template <int LANES, bool PER_X0, int TEX>
 __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, unsigned qmask,
                                             float &J, float &margin, bool &feasible)
 {
@@ -84,6 +85,7 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
         }
         bool done = false, off = false;
         const float h = p.h;
+        double J64 = 0.0;          // the running cost in FP64 when p.acc64
         float Ufrozen = 0.f;
 
         for (int k = 0; k < p.H; ++k) {
@@ -138,10 +140,10 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 // longitudinal constraint force enters My only
                 float FyB, FzB, Mx, My, Mz, csum;
                 if (LANES == 1) {
-                    const WheelOut fl = wheel(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, off);
-                    const WheelOut fr = wheel(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, off);
-                    const WheelOut rl = wheel(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, off);
-                    const WheelOut rr = wheel(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                    const WheelOut fl = wheel<TEX>(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, off);
+                    const WheelOut fr = wheel<TEX>(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, off);
+                    const WheelOut rl = wheel<TEX>(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                    const WheelOut rr = wheel<TEX>(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, off);
                     const float Fyf = (fl.Fy + fr.Fy) * cd;
                     const float Fyr = rl.Fy + rr.Fy;
                     FyB = Fyf + Fyr;
@@ -151,7 +153,7 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     Mz = fmaf(V.Lf, Fyf, -V.Lr * Fyr);
                     csum = (fl.cost + fr.cost) + (rl.cost + rr.cost);
                 } else {
-                    const WheelOut w = wheel(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, off);
+                    const WheelOut w = wheel<TEX>(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, off);
                     const float fy = front ? w.Fy * cd : w.Fy;
                     FyB = quad_sum(fy, qmask);
                     FzB = quad_sum(w.Fz, qmask);
@@ -165,7 +167,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 // running cost L = L_0 + L_soft (Sec. IV-C), left Riemann sum
                 const float soft = fmaxf(fmaf(-U, Cc.inv_eps, 1.f), 0.f);
                 const float L = fmaf(Cc.sigma * soft, soft, fmaf(Cc.wc * dd, dd, Cc.wt)) + csum;
-                J = fmaf(h, L, J);
+                if (p.acc64) J64 += (double)(h * L);
+                else J = fmaf(h, L, J);
                 // state derivative A(xi) + B zeta (Sec. IV-A)
                 const float ic = rcp(cth);
                 const float wsc = fmaf(sph, wy, cph * wz);
@@ -216,7 +219,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
             const float gdy = (y - Cc.gy_hi) + (yl - Cc.gy_lo);
             const float d2 = fmaf(gdx, gdx, gdy * gdy);
             if (!done && d2 <= Cc.goal_r2) done = true;
-            J = fmaf(Cc.wg, sqrtf(d2), J);
+            if (p.acc64) J = (float)(J64 + (double)(Cc.wg * sqrtf(d2)));
+            else J = fmaf(Cc.wg, sqrtf(d2), J);
         }
         // fold the low parts back and leave the terrain frame
         const float xs[13] = {(x + T.x0_hi) + (xl + T.x0_lo), (y + T.y0_hi) + (yl + T.y0_lo),
@@ -327,7 +331,7 @@ __device__ __forceinline__ void plan_tail(const PlanParams &p, int j, bool leade
     }
 }
 
-template <int LANES, bool PER_X0, bool REDUCE>
+template <int LANES, bool PER_X0, bool REDUCE, int TEX>
 __global__ void __launch_bounds__(kPlanBlock)
 plan_kernel(const __grid_constant__ PlanParams p)
 {
@@ -338,7 +342,7 @@ plan_kernel(const __grid_constant__ PlanParams p)
     const unsigned qmask = LANES == 1 ? 0u : (0xfu << (threadIdx.x & 28));
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
-    if (live) rollout_one<LANES, PER_X0>(p, j, q, qmask, J, margin, feasible);
+    if (live) rollout_one<LANES, PER_X0, TEX>(p, j, q, qmask, J, margin, feasible);
     if (!REDUCE) return;
     plan_tail(p, j, live && q == 0, J, feasible, gridDim.x);
 }
@@ -365,8 +369,13 @@ plan_batch_kernel(const __grid_constant__ BatchParams b)
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
     if (live) {
-        if (p.x0_soa) rollout_one<4, true>(p, j, q, qmask, J, margin, feasible);
-        else rollout_one<4, false>(p, j, q, qmask, J, margin, feasible);
+        if (p.tex_format == TEX_F32) {
+            if (p.x0_soa) rollout_one<4, true, TEX_F32>(p, j, q, qmask, J, margin, feasible);
+            else rollout_one<4, false, TEX_F32>(p, j, q, qmask, J, margin, feasible);
+        } else {
+            if (p.x0_soa) rollout_one<4, true, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
+            else rollout_one<4, false, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
+        }
     }
     plan_tail(p, j, live && q == 0, J, feasible, (unsigned)(b.cta_begin[lo + 1] - b.cta_begin[lo]));
 }
@@ -378,7 +387,7 @@ cudaError_t launch_plan_batch(const BatchParams &b, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int LANES>
+template <int LANES, int TEX>
 static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t stream)
 {
     const dim3 block(kPlanBlock);
@@ -386,11 +395,11 @@ static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t s
     const dim3 grid((unsigned)((threads + kPlanBlock - 1) / kPlanBlock));
     const bool per = p.x0_soa != nullptr;
     if (reduce) {
-        if (per) plan_kernel<LANES, true, true><<<grid, block, 0, stream>>>(p);
-        else plan_kernel<LANES, false, true><<<grid, block, 0, stream>>>(p);
+        if (per) plan_kernel<LANES, true, true, TEX><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<LANES, false, true, TEX><<<grid, block, 0, stream>>>(p);
     } else {
-        if (per) plan_kernel<LANES, true, false><<<grid, block, 0, stream>>>(p);
-        else plan_kernel<LANES, false, false><<<grid, block, 0, stream>>>(p);
+        if (per) plan_kernel<LANES, true, false, TEX><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<LANES, false, false, TEX><<<grid, block, 0, stream>>>(p);
     }
     return cudaGetLastError();
 }
@@ -405,8 +414,10 @@ int plan_lanes(int N)
 
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
 {
-    return plan_lanes(p.N) == 4 ? launch_lanes<4>(p, reduce, stream)
-                                : launch_lanes<1>(p, reduce, stream);
+    const bool four = plan_lanes(p.N) == 4;
+    if (p.tex_format == TEX_F32)
+        return four ? launch_lanes<4, TEX_F32>(p, reduce, stream) : launch_lanes<1, TEX_F32>(p, reduce, stream);
+    return four ? launch_lanes<4, TEX_BF16>(p, reduce, stream) : launch_lanes<1, TEX_BF16>(p, reduce, stream);
 }
 
 // Terrain texels (Sec. III-A numeric slope, reading Q10): height, central-
@@ -427,6 +438,71 @@ __global__ void terrain_prepare_f32_kernel(const float *__restrict__ H, const fl
     else if (j == ny - 1) gy = (c - H[r - nx + i]) * inv_cell;
     else gy = (H[r + nx + i] - H[r - nx + i]) * (0.5f * inv_cell);
     out[r + i] = make_float4(c, gx, gy, cm ? cm[r + i] : 0.f);
+}
+
+// BF16 texels.  Per 8 x 8 block a plane through the block's first node with
+// the slopes of its first row and first column (FP32, each operation rounded
+// on its own so that the plane is reproducible bit for bit); per node the
+// bf16 (round to nearest even) of the height's and the two node slopes'
+// residuals from that plane, and of the costmap value.
+__global__ void terrain_block_plane_kernel(const float *__restrict__ H, int nx, int ny, int nbx,
+                                           int nby, float4 *__restrict__ plane)
+{
+    const int bi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int bj = blockIdx.y * blockDim.y + threadIdx.y;
+    if (bi >= nbx || bj >= nby) return;
+    const int i0 = bi * 8, j0 = bj * 8;
+    const int ni = min(8, nx - i0), nj = min(8, ny - j0);
+    const float c0 = H[(size_t)j0 * nx + i0];
+    const float cx = ni > 1 ? __fmul_rn(__fsub_rn(H[(size_t)j0 * nx + i0 + ni - 1], c0),
+                                        __fdiv_rn(1.0f, (float)(ni - 1))) : 0.f;
+    const float cy = nj > 1 ? __fmul_rn(__fsub_rn(H[(size_t)(j0 + nj - 1) * nx + i0], c0),
+                                        __fdiv_rn(1.0f, (float)(nj - 1))) : 0.f;
+    plane[(size_t)bj * nbx + bi] = make_float4(c0, cx, cy, 0.f);
+}
+
+__device__ __forceinline__ unsigned bf16_bits(float v)
+{
+    return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+__global__ void terrain_prepare_bf16_kernel(const float *__restrict__ H, const float *__restrict__ cm,
+                                            int nx, int ny, float inv_cell, const float4 *__restrict__ plane,
+                                            int nbx, uint2 *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const size_t r = (size_t)j * nx;
+    const float c = H[r + i];
+    float gx, gy;
+    if (i == 0) gx = (H[r + 1] - c) * inv_cell;
+    else if (i == nx - 1) gx = (c - H[r + nx - 2]) * inv_cell;
+    else gx = (H[r + i + 1] - H[r + i - 1]) * (0.5f * inv_cell);
+    if (j == 0) gy = (H[r + nx + i] - c) * inv_cell;
+    else if (j == ny - 1) gy = (c - H[r - nx + i]) * inv_cell;
+    else gy = (H[r + nx + i] - H[r - nx + i]) * (0.5f * inv_cell);
+    const float4 P = plane[(size_t)(j >> 3) * nbx + (i >> 3)];
+    const float res = __fsub_rn(c, block_plane(P, i, j));
+    // slopes as residuals from the plane's own slopes
+    const float rgx = __fsub_rn(gx, __fmul_rn(P.y, inv_cell));
+    const float rgy = __fsub_rn(gy, __fmul_rn(P.z, inv_cell));
+    const float cv = cm ? cm[r + i] : 0.f;
+    out[r + i] = make_uint2(bf16_bits(res) | (bf16_bits(rgx) << 16), bf16_bits(rgy) | (bf16_bits(cv) << 16));
+}
+
+cudaError_t launch_terrain_prepare_bf16(const float *heights, const float *costmap, int nx, int ny,
+                                        float inv_cell, uint2 *texels, float4 *plane, cudaStream_t stream)
+{
+    const int nbx = (nx + 7) / 8, nby = (ny + 7) / 8;
+    const dim3 b1(16, 16);
+    const dim3 g1((unsigned)((nbx + 15) / 16), (unsigned)((nby + 15) / 16));
+    terrain_block_plane_kernel<<<g1, b1, 0, stream>>>(heights, nx, ny, nbx, nby, plane);
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8));
+    terrain_prepare_bf16_kernel<<<grid, block, 0, stream>>>(heights, costmap, nx, ny, inv_cell, plane, nbx,
+                                                            texels);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_terrain_prepare_f32(const float *heights, const float *costmap, int nx, int ny,

@@ -33,6 +33,8 @@ struct PlanParams {
     uint8_t *flags;           // [N] or nullptr
     float *xf;                // [13][N] or nullptr
     float *step_margin;       // [H][N] or nullptr
+    int tex_format;           // TEX_F32 or TEX_BF16
+    int acc64;                // accumulate the running cost in FP64
     // plan only
     atp_plan_out *out;
     float *best_ctrl;         // [H][2] or nullptr
@@ -60,5 +62,10 @@ static_assert(sizeof(BatchParams) <= 32764, "batch descriptors exceed the kernel
 cudaError_t launch_plan_batch(const BatchParams &b, cudaStream_t stream);
 cudaError_t launch_terrain_prepare_f32(const float *heights, const float *costmap, int nx, int ny,
                                        float inv_cell, float4 *out, cudaStream_t stream);
+cudaError_t launch_terrain_prepare_bf16(const float *heights, const float *costmap, int nx, int ny,
+                                        float inv_cell, uint2 *texels, float4 *plane, cudaStream_t stream);
+
+// byte offset of the BF16 block planes after the texels
+inline size_t bf16_base_offset(int nx, int ny) { return ((size_t)nx * ny * 8 + 255) / 256 * 256; }
 
 }  // namespace atp

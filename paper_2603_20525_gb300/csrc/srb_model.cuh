@@ -47,8 +47,16 @@ struct Cost {
     float goal_r2;
 };
 
+// Texel formats (ATP_TERRAIN_*): F32 = float4 (f, f_x, f_y, cost) per node;
+// BF16 = four bf16 per node (f - plane, f_x - plane_x, f_y - plane_y, cost)
+// with the FP32 plane (c0, cx, cy) of the node's 8 x 8 block.
+enum { TEX_F32 = 0, TEX_BF16 = 1 };
+
 struct Terrain {
-    const float4 *tex;               // (f, f_x, f_y, cost) per node, row-major
+    const float4 *tex;               // F32 texels, row-major
+    const uint2 *tex16;              // BF16 texels, row-major
+    const float4 *plane16;           // BF16 block planes [ceil(ny/8)][ceil(nx/8)]
+    int nbx;                         // blocks per row
     int nx, ny;
     float inv_cell;                  // 1 / cell
     float x0_hi, x0_lo, y0_hi, y0_lo;  // terrain origin
@@ -114,11 +122,8 @@ __device__ __forceinline__ int axis(int ic, float fc, float o, float inv_cell, i
     return i;
 }
 
-__device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a, float b)
+__device__ __forceinline__ float4 lerp4(float4 t00, float4 t10, float4 t01, float4 t11, float a, float b)
 {
-    const float4 *r0 = T.tex + (size_t)j * T.nx + i;
-    const float4 t00 = __ldg(r0), t10 = __ldg(r0 + 1);
-    const float4 t01 = __ldg(r0 + T.nx), t11 = __ldg(r0 + T.nx + 1);
     float4 o;
     float lo, hi;
     lo = fmaf(a, t10.x - t00.x, t00.x); hi = fmaf(a, t11.x - t01.x, t01.x); o.x = fmaf(b, hi - lo, lo);
@@ -126,6 +131,38 @@ __device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a
     lo = fmaf(a, t10.z - t00.z, t00.z); hi = fmaf(a, t11.z - t01.z, t01.z); o.z = fmaf(b, hi - lo, lo);
     lo = fmaf(a, t10.w - t00.w, t00.w); hi = fmaf(a, t11.w - t01.w, t01.w); o.w = fmaf(b, hi - lo, lo);
     return o;
+}
+
+// height of a block's plane (c0, cx, cy) at node (i, j): c0 + cx (i mod 8) +
+// cy (j mod 8), every operation rounded on its own
+__device__ __forceinline__ float block_plane(float4 P, int i, int j)
+{
+    return __fadd_rn(__fadd_rn(P.x, __fmul_rn(P.y, (float)(i & 7))), __fmul_rn(P.z, (float)(j & 7)));
+}
+
+// one BF16 texel decoded: height = block plane + residual
+__device__ __forceinline__ float4 texel16(const Terrain &T, int i, int j)
+{
+    const uint2 u = __ldg(T.tex16 + (size_t)j * T.nx + i);
+    const float4 P = __ldg(T.plane16 + (size_t)(j >> 3) * T.nbx + (i >> 3));
+    float4 t;
+    t.x = __fadd_rn(block_plane(P, i, j), __uint_as_float(u.x << 16));
+    t.y = __fadd_rn(__fmul_rn(P.y, T.inv_cell), __uint_as_float(u.x & 0xffff0000u));
+    t.z = __fadd_rn(__fmul_rn(P.z, T.inv_cell), __uint_as_float(u.y << 16));
+    t.w = __uint_as_float(u.y & 0xffff0000u);
+    return t;
+}
+
+template <int TEX>
+__device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a, float b)
+{
+    if (TEX == TEX_F32) {
+        const float4 *r0 = T.tex + (size_t)j * T.nx + i;
+        return lerp4(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + T.nx), __ldg(r0 + T.nx + 1), a, b);
+    } else {
+        return lerp4(texel16(T, i, j), texel16(T, i + 1, j), texel16(T, i, j + 1),
+                     texel16(T, i + 1, j + 1), a, b);
+    }
 }
 
 // What one wheel contributes to the force and moment sums.
@@ -146,6 +183,7 @@ struct Body {
 // v + w x rho, terrain below it, extension chi and rate against the local
 // slope-normal tau ~ (-f_x, -f_y, 1) (reading Q1), spring and damper with
 // liftoff, slip angle and sigmoid tire force.
+template <int TEX>
 __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const Body &B,
                                           float rx, float ry, float k, float b, float Fs,
                                           float di, bool &off)
@@ -163,7 +201,7 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     float a, bb;
     const int i = axis(B.icx, B.fcx, ox, T.inv_cell, T.nx, a, off);
     const int j = axis(B.icy, B.fcy, oy, T.inv_cell, T.ny, bb, off);
-    const float4 t = bilerp(T, i, j, a, bb);
+    const float4 t = bilerp<TEX>(T, i, j, a, bb);
     // tau in B = R^T (-f_x, -f_y, 1)
     const float tx = fmaf(-R[3], t.z, fmaf(-R[0], t.y, R[6]));
     const float ty = fmaf(-R[4], t.z, fmaf(-R[1], t.y, R[7]));

@@ -34,7 +34,8 @@ def test_version_and_sizes_without_gpu():
     ver = int(re.search(r"#define ATP_VERSION (\d+)", open(HEADER).read()).group(1))
     assert L.atp_version() == ver
     assert L.atp_terrain_bytes(1024, 1024, atp.F32X4) == 1024 * 1024 * 16
-    assert L.atp_terrain_bytes(512, 256, atp.BF16X4) == 512 * 256 * 8
+    assert L.atp_terrain_bytes(512, 256, atp.BF16X4) == 512 * 256 * 8 + 64 * 32 * 16
+    assert L.atp_terrain_bytes(13, 9, atp.BF16X4) == 1024 + 2 * 2 * 16   # 936 B -> 1024
     assert L.atp_terrain_bytes(0, 5, atp.F32X4) == 0
 
 
