@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = [os.path.join(_HERE, "srb.c"), os.path.join(_HERE, "sampler.c")]
+_SRC_CXX = [os.path.join(_HERE, "adjoint.cpp")]
 _HDR = [os.path.join(_HERE, "oracle.h")]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
@@ -33,17 +34,31 @@ BODY_FIELDS = tuple(f"R{i}" for i in range(9)) + ("gBx", "gBy", "gBz", "Fy", "Fz
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (FP64, no FMA contraction, OpenMP)."""
+    """Compile liboracle.so (FP64, no FMA contraction, OpenMP): the C model
+    and sampler with gcc, the C++ adjoint with g++."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    newest = max(os.path.getmtime(p) for p in _SRC + _HDR)
+    newest = max(os.path.getmtime(p) for p in _SRC + _SRC_CXX + _HDR)
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= newest:
         return _OUT
+    tag = f".{os.getpid()}"
+    objs = []
+    common = ["-O2", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+              "-fopenmp", "-Wall", "-Wno-unknown-pragmas", "-c"]
+    for src in _SRC:
+        o = os.path.join(os.path.dirname(_OUT), os.path.basename(src) + tag + ".o")
+        subprocess.run(["gcc", "-std=c11", *common, src, "-o", o], check=True, capture_output=True, text=True)
+        objs.append(o)
+    for src in _SRC_CXX:
+        o = os.path.join(os.path.dirname(_OUT), os.path.basename(src) + tag + ".o")
+        subprocess.run(["g++", "-std=c++17", *common, src, "-o", o], check=True, capture_output=True,
+                       text=True)
+        objs.append(o)
     tmp = _OUT + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
-           "-fno-fast-math", "-fPIC", "-shared", "-fopenmp", "-Wall", "-Wno-unknown-pragmas",
-           *_SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    subprocess.run(["g++", "-shared", "-fopenmp", *objs, "-o", tmp, "-lm"], check=True,
+                   capture_output=True, text=True)
     os.replace(tmp, _OUT)
+    for o in objs:
+        os.remove(o)
     return _OUT
 
 
@@ -98,6 +113,16 @@ def lib():
             L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
             L.orc_sample.argtypes = [_fp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                      C.c_uint64, C.c_uint64, C.c_int, C.c_int, _dp]
+            L.orc_cost_templated.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                             _dp, _fp, C.c_int, C.c_double, C.c_int]
+            L.orc_cost_templated.restype = C.c_double
+            L.orc_cost_f64.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                       _dp, _dp, C.c_int, C.c_double, C.c_int]
+            L.orc_cost_f64.restype = C.c_double
+            L.orc_grad_batch.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                         _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                         _dp, _dp]
+            L.orc_grad_batch.restype = C.c_int
             _lib = L
     return _lib
 
@@ -301,3 +326,35 @@ def bf16_terrain(heights, cell):
     gx_dec = (px + bf16_value(w_gx)).astype(np.float32)
     gy_dec = (py + bf16_value(w_gy)).astype(np.float32)
     return (h_dec, gx_dec.astype(np.float64), gy_dec.astype(np.float64), (w_res, w_gx, w_gy), plane)
+
+
+def cost_templated(veh: dict, cst: dict, ter: Terrain, x0, ctrl_h2, dt: float, n_sub: int):
+    """J of one candidate through the adjoint's templated model (FP64)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    ctrl_h2 = np.ascontiguousarray(ctrl_h2, dtype=np.float32)
+    return lib().orc_cost_templated(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                                    _ptr(x0, _dp), _ptr(ctrl_h2, _fp), ctrl_h2.shape[0], float(dt),
+                                    int(n_sub))
+
+
+def grad(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int):
+    """J [N] and dJ/du [H, N, 2] by FP64 reverse-mode AD (adjoint.cpp)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
+    H, N, _ = ctrl.shape
+    J = np.empty(N)
+    G = np.empty((H, N, 2))
+    rc = lib().orc_grad_batch(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                              _ptr(x0, _fp), 1 if x0.ndim == 2 else 0, _ptr(ctrl, _fp), N, H,
+                              float(dt), int(n_sub), _ptr(J, _dp), _ptr(G, _dp))
+    if rc != 0:
+        raise ValueError("oracle grad rejected its arguments")
+    return J, G
+
+
+def cost_f64(veh: dict, cst: dict, ter: Terrain, x0, u, dt: float, n_sub: int):
+    """J of one candidate with FP64 controls u [H, 2] (for finite differences)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_cost_f64(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                              _ptr(x0, _dp), _ptr(u, _dp), u.shape[0], float(dt), int(n_sub))
