@@ -238,6 +238,22 @@ typedef struct {
  * totals.  Validation failures name the offending request in atp_last_error. */
 int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *stream);
 
+/* Gradient of each candidate's cost with respect to its raw controls: the
+ * hand-written reverse-mode adjoint of the discrete rollout (Sec. IV-A..C)
+ * for K candidates, J = sum over Euler steps of h L + Phi, with the
+ * branches (liftoff, clamps, off-map, goal) taken as in the forward pass.
+ *   ctrl_dev  float2 [H][K] raw controls (steering rate, acceleration)
+ *   cost_dev  float [K]: J of each candidate (as atp_plan computes it)
+ *   grad_dev  float [H][K][2]: dJ/d(steering rate), dJ/d(acceleration);
+ *             zero for a steering rate beyond its limit (the clamp)
+ *   ckpt      control steps between stored states (0 selects 10); the
+ *             reverse pass recomputes one such segment at a time, so memory
+ *             is (H / ckpt + ckpt n_sub) x 80 bytes per candidate.
+ * One thread per candidate; F32X4 terrain only. */
+int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
+             const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int K, int H, float dt,
+             int n_sub, int ckpt, float *cost_dev, float *grad_dev, void *stream);
+
 /* Candidate sampler (the on-GPU drawing of Sec. IV-D): writes float2
  * ctrl[H][N] with ctrl[k][j] = nominal[k] + (sigma_rate n1, sigma_acc n2),
  * where (n1, n2) is the Box-Muller pair of two 23-bit uniforms taken from the

@@ -27,7 +27,7 @@ FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
            "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch",
-           "atp_set_option")
+           "atp_set_option", "atp_grad")
 
 
 class Vehicle(C.Structure):
@@ -107,11 +107,14 @@ def load(build_if_missing: bool = True):
         L.atp_math_check.argtypes = [_vp, _vp, C.c_int, _vp, _vp]
         L.atp_plan_batch.argtypes = [_vp, C.POINTER(PlanRequest), C.c_int, _vp]
         L.atp_set_option.argtypes = [_vp, C.c_int, C.c_int]
+        L.atp_grad.argtypes = [_vp, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
+                               C.POINTER(State), _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
+                               C.c_int, _vp, _vp, _vp]
         L.atp_sample.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_int, C.c_int, _vp, _vp]
         for n in ("atp_create", "atp_destroy", "atp_reserve", "atp_terrain_prepare",
                   "atp_plan", "atp_rollout", "atp_plan_noalloc", "atp_math_check", "atp_sample",
-                  "atp_plan_batch", "atp_set_option"):
+                  "atp_plan_batch", "atp_set_option", "atp_grad"):
             getattr(L, n).restype = C.c_int
         _lib = L
         return L
@@ -253,6 +256,21 @@ class Context:
         rc = self.lib.atp_plan_batch(self.h, arr, n, _stream(stream))
         self._check(rc, "atp_plan_batch")
         return [q["out"] for q in requests]
+
+    def grad(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0, ckpt=10,
+             stream=None):
+        """J [K] and dJ/dctrl [H, K, 2] of K candidates (atp_grad)."""
+        import torch
+        H, K, _ = ctrl.shape
+        J = torch.empty(K, dtype=torch.float32, device=ctrl.device)
+        G = torch.empty((H, K, 2), dtype=torch.float32, device=ctrl.device)
+        xs, xdev = (None, x0) if isinstance(x0, torch.Tensor) else (state(x0), None)
+        rc = self.lib.atp_grad(self.h, C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(terrain.c),
+                               C.byref(xs) if xs is not None else None, _ptr(xdev), _ptr(ctrl),
+                               int(K), int(H), float(dt), int(n_sub), int(ckpt), _ptr(J), _ptr(G),
+                               _stream(stream))
+        self._check(rc, "atp_grad")
+        return J, G
 
     def sample(self, N, H, sigma_rate, sigma_acc, key, nonce, prev=None, shift=1, out=None,
                stream=None):

@@ -1,0 +1,27 @@
+// adjoint.cuh - parameters of the rollout-cost adjoint kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "srb_model.cuh"
+
+namespace atp {
+
+struct GradParams {
+    Veh V;
+    Cost C;
+    Terrain T;
+    float x0[13];             // shared initial state (x0_soa == nullptr)
+    const float *x0_soa;      // [13][K] or nullptr
+    const float2 *ctrl;       // [H][K]
+    int K, H, n_sub, ckpt;
+    float h;
+    float *cost;              // [K]
+    float *grad;              // [H][K][2]
+    float *ckpt_buf;          // [ceil(H / ckpt)][20][K]
+    float *seg_buf;           // [ckpt * n_sub][20][K]
+};
+
+cudaError_t launch_grad(const GradParams &p, cudaStream_t stream);
+
+}  // namespace atp

@@ -10,6 +10,7 @@
 #include <new>
 
 #include "atp.h"
+#include "adjoint.cuh"
 #include "plan_kernel.cuh"
 #include "sampler.cuh"
 
@@ -521,6 +522,54 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
     }
     cudaError_t e = atp::launch_plan_batch(b, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch launch");
+    return ATP_OK;
+}
+
+extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                        const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
+                        const float *ctrl_dev, int K, int H, float dt, int n_sub, int ckpt,
+                        float *cost_dev, float *grad_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int ns = 0;
+    int rc = common_checks(ctx, veh, cost, terrain, x0, x0_dev, ctrl_dev, K, H, dt, n_sub, &ns);
+    if (rc != ATP_OK) return rc;
+    if (terrain->format != ATP_TERRAIN_F32X4)
+        return fail(ctx, ATP_ERR_UNSUPPORTED, "the adjoint takes F32X4 terrain only");
+    if (!cost_dev || !grad_dev) return fail(ctx, ATP_ERR_INVALID, "cost_dev and grad_dev are required");
+    if (ckpt == 0) ckpt = 10;
+    if (ckpt < 1) return fail(ctx, ATP_ERR_INVALID, "ckpt must be >= 1 (0 selects 10)");
+    if (ckpt > H) ckpt = H;
+    const size_t n_seg = (size_t)(H + ckpt - 1) / ckpt;
+    const size_t ck_bytes = align_up(n_seg * 20 * (size_t)K * sizeof(float));
+    const size_t seg_bytes = align_up((size_t)ckpt * ns * 20 * (size_t)K * sizeof(float));
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    if ((rc = ensure_scratch_bytes(ctx, ck_bytes + seg_bytes)) != ATP_OK) return rc;
+    char *base = (char *)ctx->scratch + kHeaderBytes;
+    atp::PlanParams pp;
+    std::memset(&pp, 0, sizeof pp);
+    derive(*veh, *cost, *terrain, pp);
+    fill_problem(pp, x0, x0_dev, ctrl_dev, K, H, dt, ns);
+    atp::GradParams p;
+    std::memset(&p, 0, sizeof p);
+    p.V = pp.V;
+    p.C = pp.C;
+    p.T = pp.T;
+    std::memcpy(p.x0, pp.x0, sizeof p.x0);
+    p.x0_soa = pp.x0_soa;
+    p.ctrl = pp.ctrl;
+    p.K = K;
+    p.H = H;
+    p.n_sub = ns;
+    p.ckpt = ckpt;
+    p.h = pp.h;
+    p.cost = cost_dev;
+    p.grad = grad_dev;
+    p.ckpt_buf = (float *)base;
+    p.seg_buf = (float *)(base + ck_bytes);
+    cudaError_t e = atp::launch_grad(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "grad launch");
     return ATP_OK;
 }
 
