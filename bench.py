@@ -142,6 +142,8 @@ def make_workload(name):
         return gen.workload_scaled(0)
     if name == "plain":
         return gen.workload_plain(0)
+    if name == "paper":
+        return gen.workload_paper(0)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -151,7 +153,8 @@ def workload_config(w, name):
                         f"{w.terrain.nx}x{w.terrain.ny} heightmap at {w.terrain.cell} m",
             "candidates": w.N, "horizon": w.H, "dt": w.dt, "n_sub": w.n_sub,
             "terrain": [w.terrain.ny, w.terrain.nx], "cell_m": w.terrain.cell,
-            "vehicle": "1000 kg, wheelbase 2.5 m, track 1.5 m, CoM 0.6 m, 40 kN/m, 3 kN s/m",
+            "vehicle": ("MRZR parameters (appendix)" if name == "paper" else
+                        "1000 kg, wheelbase 2.5 m, track 1.5 m, CoM 0.6 m, 40 kN/m, 3 kN s/m"),
             "l2": "flushed between steps (256 MB write)"}
 
 
@@ -203,6 +206,39 @@ def cpu_baseline(w, budget_s=10.0):
             "sample": f"{n} whole plans of the workload ({n * w.N} candidates, {el:.1f} s), FP64"}
 
 
+def run_paper_config(ctx, dev, stream, flush, steps=10, warmup=3):
+    """The real-time configuration of Sec. IV-D (204,288 candidates, 16 steps
+    of 0.25 s, 800 Euler steps of 5 ms each, steering only) on this GPU, in
+    the paper's units: trajectory samples per second and the planner rate.
+    The paper's own figures on its hardware are quoted beside it."""
+    import gen
+    import torch
+    w = gen.workload_paper(0)
+    ter = ctx.terrain_prepare(torch.as_tensor(w.terrain.heights).to(dev), w.terrain.cell,
+                              w.terrain.x0, w.terrain.y0)
+    ctrl = torch.as_tensor(w.ctrl).to(dev)
+    x0 = [float(v) for v in w.x0]
+    outs = ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False)
+    for _ in range(warmup):
+        ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, out=outs)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, out=outs)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    return {"workload": f"{w.N} candidates x 16 steps of 0.25 s ({w.n_sub} Euler steps of 5 ms "
+                        f"each), steering only, {w.terrain.nx}^2 heightmap at {w.terrain.cell} m",
+            "ms_per_plan": ms, "planner_hz": 1000.0 / ms, "samples_per_s": w.N / (ms / 1000),
+            "substeps_per_s": w.N * w.H * w.n_sub / (ms / 1000),
+            "paper_context": "80 Hz, over 11 M samples/s on an RTX 5000 Ada Mobile; about 21 M "
+                             "samples/s on an RTX 6000 Ada (Sec. IV-D); other hardware"}
+
+
 def run_serving(seconds, device):
     """The serving stream: 32 vehicles, each on its own resident 512-2048^2
     tile, Poisson plan requests at 20 Hz per vehicle with N in {1k, 4k, 16k,
@@ -236,7 +272,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scaled", choices=["scaled", "plain"])
+    ap.add_argument("--workload", default="scaled", choices=["scaled", "plain", "paper"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="seconds of the 32-vehicle request stream (0: skip)")
@@ -361,6 +397,8 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
         }
+        if args.workload != "paper":
+            line["paper_configuration"] = run_paper_config(ctx, dev, stream, flush)
         if args.serve_seconds > 0:
             line["serving"] = run_serving(args.serve_seconds, local)
         if not args.no_cpu_baseline and ws == 1:

@@ -386,3 +386,25 @@ def fleet(n: int = 32, seed: int = 0, sides=(512, 1024, 2048)):
         cost = cost_default(x + 40.0 * math.cos(psi), y + 40.0 * math.sin(psi))
         out.append(FleetVehicle(t, veh, cost, x0, (seed + 1, v + 1)))
     return out
+
+
+def candidates_uniform(N: int, H: int, seed: int, rate_max: float = 1.0) -> np.ndarray:
+    """The paper's sampling (Sec. IV-D, V): i.i.d. uniform steering rates over
+    the admissible set |delta_dot| <= rate_max, zero longitudinal
+    acceleration; float32 [H, N, 2]."""
+    u = np.zeros((H, N, 2), dtype=np.float64)
+    u[..., 0] = rate_max * (2.0 * uniform(seed, 23, H * N).reshape(H, N) - 1.0)
+    return u.astype(np.float32)
+
+
+def workload_paper(seed: int = 0, N: int = 204288) -> Workload:
+    """The paper's real-time configuration (Sec. IV-D): N = 204,288 candidates
+    of 16 zero-order-hold steps of 0.25 s (a 4 s horizon, 800 Euler steps of
+    5 ms), steering only, on the scaled 1024^2 terrain, MRZR vehicle at
+    7.5 m/s."""
+    ter = terrain_scaled(seed)
+    veh = vehicle_mrzr()
+    x0 = settled_state(ter, veh, 10.0, 51.2, 0.0, 7.5)
+    ctrl = candidates_uniform(N, 16, seed)
+    return Workload(f"paper-{N}x16", ter, veh, cost_default(95.0, 51.2), x0, ctrl, 0.25,
+                    n_sub=50, meta=dict(seed=seed))

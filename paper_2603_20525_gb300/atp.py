@@ -21,6 +21,7 @@ ERRORS = {-1: "ATP_ERR_INVALID", -2: "ATP_ERR_UNSUPPORTED", -3: "ATP_ERR_NOMEM",
           -4: "ATP_ERR_CUDA", -5: "ATP_ERR_TIMEOUT"}
 F32X4, BF16X4 = 0, 1
 OPT_COST_FP64 = 1
+OPT_LANES = 2
 FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
 
 # every symbol include/atp.h declares

@@ -17,6 +17,7 @@
 struct atp_ctx {
     int device;
     int acc64;                // ATP_OPT_COST_FP64
+    int lanes;                // ATP_OPT_LANES
     char err[256];
     void *scratch;            // reduction headers + per-plan candidate buffers
     size_t scratch_bytes;
@@ -304,6 +305,7 @@ int atp_create(atp_ctx **out, int device)
     if (!ctx) return ATP_ERR_NOMEM;
     ctx->device = device;
     ctx->acc64 = 0;
+    ctx->lanes = 0;
     ctx->err[0] = 0;
     ctx->batch = new (std::nothrow) atp::BatchParams;
     if (!ctx->batch) {
@@ -364,6 +366,12 @@ int atp_set_option(atp_ctx *ctx, int option, int value)
     if (!ctx) return ATP_ERR_INVALID;
     if (option == ATP_OPT_COST_FP64) {
         ctx->acc64 = value != 0;
+        return ATP_OK;
+    }
+    if (option == ATP_OPT_LANES) {
+        if (value != 0 && value != 1 && value != 4)
+            return fail(ctx, ATP_ERR_INVALID, "ATP_OPT_LANES takes 0, 1 or 4");
+        ctx->lanes = value;
         return ATP_OK;
     }
     return fail(ctx, ATP_ERR_INVALID, "unknown option %d", option);
@@ -436,6 +444,7 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     p.best_margin = best_margin_dev;
     p.scratch = (atp::Scratch *)ctx->scratch;
     p.acc64 = ctx->acc64;
+    p.lanes = ctx->lanes;
     cudaError_t e = atp::launch_plan(p, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
     return ATP_OK;
@@ -462,6 +471,7 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
     p.xf = cand_xf_dev;
     p.step_margin = step_margin_dev;
     p.acc64 = ctx->acc64;
+    p.lanes = ctx->lanes;
     cudaError_t e = atp::launch_plan(p, false, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
     return ATP_OK;
@@ -489,7 +499,7 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
         if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
         need += region_layout((size_t)q.N, (size_t)q.H).total;
-        ctas += ((long long)q.N * 4 + atp::kPlanBlock - 1) / atp::kPlanBlock;
+        ctas += ((long long)q.N * atp::plan_lanes(ctx->lanes, q.N) + atp::kPlanBlock - 1) / atp::kPlanBlock;
     }
     if (ctas > 0x7fffffffLL) return fail(ctx, ATP_ERR_UNSUPPORTED, "batch too large");
     DeviceGuard g(ctx->device);
@@ -517,8 +527,9 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         p.best_margin = q.best_margin_dev;
         p.scratch = (atp::Scratch *)ctx->scratch + r;
         p.acc64 = ctx->acc64;
+        p.lanes = atp::plan_lanes(ctx->lanes, q.N);
         region += L.total;
-        b.cta_begin[r + 1] = b.cta_begin[r] + (q.N * 4 + atp::kPlanBlock - 1) / atp::kPlanBlock;
+        b.cta_begin[r + 1] = b.cta_begin[r] + (int)(((long long)q.N * p.lanes + atp::kPlanBlock - 1) / atp::kPlanBlock);
     }
     cudaError_t e = atp::launch_plan_batch(b, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch launch");

@@ -349,9 +349,10 @@ plan_kernel(const __grid_constant__ PlanParams p)
 
 // Continuous batching: one launch over a ragged batch of plans, each with its
 // own vehicle, terrain, horizon, candidates and outputs.  Plan r owns CTAs
-// [cta_begin[r], cta_begin[r+1]) with four lanes per candidate; every
-// candidate runs exactly the code of a single plan, so its results are the
-// same bits alone and in any mix.
+// [cta_begin[r], cta_begin[r+1]) with p.lanes (1 or 4, chosen by the same
+// rule as a single plan) threads per candidate; every candidate runs exactly
+// the code of a single plan, so its results are the same bits alone and in
+// any mix.
 __global__ void __launch_bounds__(kPlanBlock)
 plan_batch_kernel(const __grid_constant__ BatchParams b)
 {
@@ -363,18 +364,30 @@ plan_batch_kernel(const __grid_constant__ BatchParams b)
     }
     const PlanParams &p = b.req[lo];
     const int tid = ((int)blockIdx.x - b.cta_begin[lo]) * kPlanBlock + (int)threadIdx.x;
-    const int j = tid >> 2, q = tid & 3;
+    // every thread of a CTA belongs to one plan: the branch is CTA-uniform
+    const bool four = p.lanes == 4;
+    const int j = four ? tid >> 2 : tid, q = four ? tid & 3 : 0;
     const bool live = j < p.N;
-    const unsigned qmask = 0xfu << (threadIdx.x & 28);
+    const unsigned qmask = four ? 0xfu << (threadIdx.x & 28) : 0u;
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
     if (live) {
-        if (p.tex_format == TEX_F32) {
-            if (p.x0_soa) rollout_one<4, true, TEX_F32>(p, j, q, qmask, J, margin, feasible);
-            else rollout_one<4, false, TEX_F32>(p, j, q, qmask, J, margin, feasible);
+        if (four) {
+            if (p.tex_format == TEX_F32) {
+                if (p.x0_soa) rollout_one<4, true, TEX_F32>(p, j, q, qmask, J, margin, feasible);
+                else rollout_one<4, false, TEX_F32>(p, j, q, qmask, J, margin, feasible);
+            } else {
+                if (p.x0_soa) rollout_one<4, true, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
+                else rollout_one<4, false, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
+            }
         } else {
-            if (p.x0_soa) rollout_one<4, true, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
-            else rollout_one<4, false, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
+            if (p.tex_format == TEX_F32) {
+                if (p.x0_soa) rollout_one<1, true, TEX_F32>(p, j, 0, 0u, J, margin, feasible);
+                else rollout_one<1, false, TEX_F32>(p, j, 0, 0u, J, margin, feasible);
+            } else {
+                if (p.x0_soa) rollout_one<1, true, TEX_BF16>(p, j, 0, 0u, J, margin, feasible);
+                else rollout_one<1, false, TEX_BF16>(p, j, 0, 0u, J, margin, feasible);
+            }
         }
     }
     plan_tail(p, j, live && q == 0, J, feasible, (unsigned)(b.cta_begin[lo + 1] - b.cta_begin[lo]));
@@ -404,17 +417,12 @@ static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t s
     return cudaGetLastError();
 }
 
-int plan_lanes(int N)
-{
-    // four lanes per candidate while the batch leaves the GPU's thread
-    // slots mostly empty (the rollout is then latency bound); one lane when
-    // the batch alone fills the machine
-    return N <= kLanes4MaxN ? 4 : 1;
-}
-
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
 {
-    const bool four = plan_lanes(p.N) == 4;
+    // four lanes per candidate while the batch leaves the GPU's thread slots
+    // mostly empty (the rollout is then latency bound); one lane once the
+    // batch fills the machine
+    const bool four = plan_lanes(p.lanes, p.N) == 4;
     if (p.tex_format == TEX_F32)
         return four ? launch_lanes<4, TEX_F32>(p, reduce, stream) : launch_lanes<1, TEX_F32>(p, reduce, stream);
     return four ? launch_lanes<4, TEX_BF16>(p, reduce, stream) : launch_lanes<1, TEX_BF16>(p, reduce, stream);

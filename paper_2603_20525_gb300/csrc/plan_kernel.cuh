@@ -35,6 +35,7 @@ struct PlanParams {
     float *step_margin;       // [H][N] or nullptr
     int tex_format;           // TEX_F32 or TEX_BF16
     int acc64;                // accumulate the running cost in FP64
+    int lanes;                // 0: by batch size; 1 or 4 lanes per candidate
     // plan only
     atp_plan_out *out;
     float *best_ctrl;         // [H][2] or nullptr
@@ -43,10 +44,12 @@ struct PlanParams {
 };
 
 constexpr int kPlanBlock = 64;
-// largest batch that runs four lanes (one wheel each) per candidate
-constexpr int kLanes4MaxN = 1 << 17;
+// largest batch that runs four lanes (one wheel each) per candidate; above
+// it one lane per candidate gives more rollouts per second on a 152-SM GPU
+constexpr int kLanes4MaxN = 1 << 14;
 
-int plan_lanes(int N);
+// threads per candidate: `forced` (1 or 4) if set, else by batch size
+inline int plan_lanes(int forced, int N) { return forced ? forced : (N <= kLanes4MaxN ? 4 : 1); }
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream);
 
 // A ragged batch of plans in one launch.  The descriptors travel in the

@@ -55,6 +55,9 @@ def requests_mix():
     rs.append(dict(w=w, x0=x0, name="tile-4096"))
     w = gen.workload_scaled(1, N=2048, H=30)
     rs.append(dict(w=w, x0=w.x0, name="scaled-2048"))
+    # above the four-lane limit: one thread per candidate inside the batch
+    w = gen.workload_scaled(2, N=20000, H=12, terrain=w.terrain)
+    rs.append(dict(w=w, x0=w.x0, name="scaled-20000"))
     return rs
 
 
@@ -105,7 +108,7 @@ def test_alone_and_in_any_mix_bitwise(ctx):
     alone = {k: v.clone() for k, v in target["out"].items()}
     rng = np.random.default_rng(0)
     for trial in range(4):
-        others = [qs[i] for i in rng.permutation([0, 1, 3])[: trial + 1]]
+        others = [qs[i] for i in rng.permutation([0, 1, 3, 4])[: trial + 1]]
         mix = others + [target] if trial % 2 else [target] + others
         for q in mix:
             q["out"] = fresh_outputs(q)
