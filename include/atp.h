@@ -239,8 +239,8 @@ typedef struct {
 /* Continuous batching: n_req (1..64) independent plans, each with its own
  * vehicle, terrain, candidates, horizon and outputs, in one kernel launch.
  * Each plan's results are bit-identical to a single atp_plan of the same
- * request for N <= 131072 (both run four lanes per candidate), alone or in
- * any mix.  The context's scratch grows to the sum of the plans' needs;
+ * request on a context with the same ATP_OPT_LANES (both choose the threads
+ * per candidate by the same rule), alone or in any mix.  The context's scratch grows to the sum of the plans' needs;
  * atp_reserve(ctx, sum of N, max H) pre-sizes it for any batch within those
  * totals.  Validation failures name the offending request in atp_last_error. */
 int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *stream);

@@ -17,7 +17,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "srb.c"), os.path.join(_HERE, "sampler.c")]
+_SRC = [os.path.join(_HERE, n) for n in ("srb.c", "sampler.c", "est.c", "terrain_tools.c")]
 _SRC_CXX = [os.path.join(_HERE, "adjoint.cpp")]
 _HDR = [os.path.join(_HERE, "oracle.h")]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
@@ -123,6 +123,25 @@ def lib():
                                          _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double, C.c_int,
                                          _dp, _dp]
             L.orc_grad_batch.restype = C.c_int
+            L.orc_est_rotation.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+            L.orc_est_eval.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                       _dp, _dp, _dp, _dp]
+            L.orc_est_rollout.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                          _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                          _dp, _dp, _up, _dp, _dp, _dp, C.c_int]
+            L.orc_est_rollout.restype = C.c_int
+            L.orc_est_trajectory.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                             _dp, _fp, C.c_int, C.c_double, C.c_int, _dp]
+            L.orc_est_trajectory.restype = C.c_int
+            L.orc_lod_weights.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
+            L.orc_lod_weights.restype = C.c_int
+            L.orc_lod_smooth.argtypes = [_fp, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
+            L.orc_lod_smooth.restype = C.c_int
+            _ip = C.POINTER(C.c_int)
+            L.orc_sdist.argtypes = [_dp, C.c_int, C.c_int, C.c_double, C.c_double]
+            L.orc_sdist.restype = C.c_double
+            L.orc_costmap.argtypes = [_dp, _ip, _ip, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, C.c_double, _dp, _dp]
             _lib = L
     return _lib
 
@@ -358,3 +377,128 @@ def cost_f64(veh: dict, cst: dict, ter: Terrain, x0, u, dt: float, n_sub: int):
     u = np.ascontiguousarray(u, dtype=np.float64)
     return lib().orc_cost_f64(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
                               _ptr(x0, _dp), _ptr(u, _dp), u.shape[0], float(dt), int(n_sub))
+
+
+# ---- Extended single-track (EST) planar model --------------------------------
+EST_FIELDS = ("theta", "phi", "gBx", "gBy", "gBz", "aBx", "Fzf", "Fzr", "alpha_f", "alpha_r",
+              "Fyf", "Fyr", "aBy", "margin", "L", "cm_fl", "cm_fr", "cm_rl", "cm_rr")
+
+
+def est_rotation(phi, theta, psi):
+    R = np.empty(9)
+    lib().orc_est_rotation(float(phi), float(theta), float(psi), _ptr(R, _dp))
+    return R.reshape(3, 3)
+
+
+def est_evaluate(veh: dict, cst: dict, ter: Terrain, xi, zeta):
+    """EST xi_dot [7] and the diagnostics named by EST_FIELDS."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    zeta = np.ascontiguousarray(zeta, dtype=np.float64)
+    xd = np.empty(7)
+    d = np.empty(len(EST_FIELDS))
+    lib().orc_est_eval(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c), _ptr(xi, _dp),
+                       _ptr(zeta, _dp), _ptr(xd, _dp), _ptr(d, _dp))
+    return xd, dict(zip(EST_FIELDS, d))
+
+
+def est_rollout(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int,
+                want_xf=True, want_step_margin=False, want_diag=True, nthreads=0):
+    """EST rollout of every candidate.  x0 float32 [7] or [N, 7]; ctrl float32 [H, N, 2]."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
+    H, N, _ = ctrl.shape
+    per = 1 if x0.ndim == 2 else 0
+    if per:
+        assert x0.shape == (N, 7)
+    J = np.empty(N)
+    margin = np.empty(N)
+    flags = np.empty(N, dtype=np.uint8)
+    xf = np.empty((N, 7)) if want_xf else None
+    sm = np.empty((H, N)) if want_step_margin else None
+    diag = np.empty((N, 3)) if want_diag else None
+    rc = lib().orc_est_rollout(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                               _ptr(x0, _fp), per, _ptr(ctrl, _fp), N, H, float(dt), int(n_sub),
+                               _ptr(J, _dp), _ptr(margin, _dp), _ptr(flags, _up),
+                               _ptr(xf, _dp), _ptr(sm, _dp), _ptr(diag, _dp), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle EST rollout rejected its arguments")
+    return dict(J=J, margin=margin, flags=flags, xf=xf, step_margin=sm, diag=diag)
+
+
+def est_plan(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int, nthreads=0):
+    """EST rollout, empirical argmin and the best candidate's outputs."""
+    r = est_rollout(veh, cst, ter, x0, ctrl, dt, n_sub, want_step_margin=True, nthreads=nthreads)
+    b = select(r["J"], r["flags"])
+    ctrl = np.asarray(ctrl, dtype=np.float32)
+    best_ctrl = ctrl[:, b, :].astype(np.float64)
+    best_ctrl[:, 0] = np.clip(best_ctrl[:, 0], -veh["delta_rate_max"], veh["delta_rate_max"])
+    r.update(best=b, n_feasible=int(np.count_nonzero(r["flags"] & FEASIBLE)),
+             best_cost=float(r["J"][b]), best_margin=float(r["margin"][b]),
+             best_ctrl=best_ctrl, best_step_margin=r["step_margin"][:, b].copy())
+    return r
+
+
+def est_trajectory(veh: dict, cst: dict, ter: Terrain, x0, ctrl_h2, dt: float, n_sub: int):
+    """One EST candidate with every Euler state: [H n_sub + 1, 7]."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    ctrl_h2 = np.ascontiguousarray(ctrl_h2, dtype=np.float32)
+    H = ctrl_h2.shape[0]
+    states = np.empty((H * n_sub + 1, 7))
+    lib().orc_est_trajectory(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                             _ptr(x0, _dp), _ptr(ctrl_h2, _fp), H, float(dt), int(n_sub),
+                             _ptr(states, _dp))
+    return states
+
+
+def est_state_of(x13):
+    """EST state (x, y, psi, v_By, w_Bz, delta, v_Bx) of an SRB state."""
+    x13 = np.asarray(x13)
+    return x13[..., [0, 1, 3, 7, 11, 12, 6]]
+
+
+# ---- Terrain preprocessing ----------------------------------------------------
+def lod_weights(cell: float, sigma: float):
+    w = np.empty(2 * 4096 + 1)
+    r = lib().orc_lod_weights(float(cell), float(sigma), 4096, _ptr(w, _dp))
+    if r < 0:
+        raise ValueError("kernel radius above 4096 cells")
+    return w[: 2 * r + 1].copy()
+
+
+def lod_smooth(heights, cell: float, sigma: float):
+    """Gaussian level of detail of a heightmap, FP64 [ny, nx]."""
+    f = np.ascontiguousarray(heights, dtype=np.float32)
+    out = np.empty(f.shape)
+    if lib().orc_lod_smooth(_ptr(f, _fp), f.shape[1], f.shape[0], float(cell), float(sigma),
+                            _ptr(out, _dp)) != 0:
+        raise ValueError("kernel radius above 4096 cells")
+    return out
+
+
+def _perimeters(polys):
+    xy = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).reshape(-1, 2) for p, _ in polys]))
+    start = np.zeros(len(polys) + 1, dtype=np.int32)
+    start[1:] = np.cumsum([len(np.asarray(p).reshape(-1, 2)) for p, _ in polys])
+    kind = np.ascontiguousarray([k for _, k in polys], dtype=np.int32)
+    return xy, start, kind
+
+
+def sdist(poly, kind: int, px: float, py: float) -> float:
+    """Signed distance to one closed perimeter: kind 0 obstacle (negative
+    inside), kind 1 path boundary (negative outside)."""
+    xy = np.ascontiguousarray(np.asarray(poly, np.float64).reshape(-1, 2))
+    return lib().orc_sdist(_ptr(xy, _dp), len(xy), int(kind), float(px), float(py))
+
+
+def costmap(polys, nx: int, ny: int, cell: float, x0: float, y0: float, eps: float = 0.25,
+            sigma: float = 1e6):
+    """Summed distance-constraint cost rate at every node and the smallest
+    signed distance; polys is a list of (vertices [n, 2], kind)."""
+    xy, start, kind = _perimeters(polys)
+    c = np.empty((ny, nx))
+    s = np.empty((ny, nx))
+    _ip = C.POINTER(C.c_int)
+    lib().orc_costmap(_ptr(xy, _dp), _ptr(start, _ip), _ptr(kind, _ip), len(polys), int(nx), int(ny),
+                      float(cell), float(x0), float(y0), float(eps), float(sigma), _ptr(c, _dp),
+                      _ptr(s, _dp))
+    return c, s

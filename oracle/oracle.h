@@ -117,6 +117,31 @@ int orc_trajectory(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t
 /* Empirical argmin (Sec. IV-D) by the lexicographic key (infeasible, J, j). */
 int orc_select(const double *J, const unsigned char *flags, int N);
 
+/* ---- Extended single-track (EST) planar model (est.c) ----------------- */
+/* EST state: x, y, psi, v_By, w_Bz, delta, v_Bx (the paper's order). */
+#define ORC_EST_FIELDS 19
+void orc_est_rotation(double phi, double theta, double psi, double R[9]);
+void orc_est_eval(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const double xi[7],
+                  const double zeta[2], double xidot[7], double *diag);
+/* As orc_rollout with 7-component states; margin = min over the integrated
+ * Euler steps of abar - |a_By - g_By|; diag[N][3] = (inf, min |margin| / abar,
+ * goal-circle distance). */
+int orc_est_rollout(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const float *x0,
+                    int x0_per_cand, const float *ctrl, int N, int H, double dt, int n_sub, double *J,
+                    double *margin, unsigned char *flags, double *xf, double *step_margin, double *diag,
+                    int nthreads);
+int orc_est_trajectory(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t,
+                       const double x0[7], const float *ctrl, int H, double dt, int n_sub,
+                       double *states);
+
+/* ---- Terrain preprocessing (terrain_tools.c) --------------------------- */
+int orc_lod_weights(double cell, double sigma, int r_max, double *w);
+int orc_lod_smooth(const float *f, int nx, int ny, double cell, double sigma, double *out);
+double orc_sdist(const double *xy, int n, int kind, double px, double py);
+void orc_costmap(const double *xy, const int *start, const int *kind, int n_poly, int nx, int ny,
+                 double cell, double x0, double y0, double eps, double sigma, double *cost,
+                 double *sdist_min);
+
 #ifdef __cplusplus
 }
 #endif
