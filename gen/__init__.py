@@ -408,3 +408,45 @@ def workload_paper(seed: int = 0, N: int = 204288) -> Workload:
     ctrl = candidates_uniform(N, 16, seed)
     return Workload(f"paper-{N}x16", ter, veh, cost_default(95.0, 51.2), x0, ctrl, 0.25,
                     n_sub=50, meta=dict(seed=seed))
+
+
+def obstacles(terrain: Terrain, seed: int, n: int = 4, path_margin: float = 4.0):
+    """Perimeters for the distance constraints (Sec. IV-C): n convex polygonal
+    obstacles (5 to 9 vertices on a jittered circle of radius 0.6-1.5 m)
+    scattered over the middle of the map, and one path boundary, the map
+    shrunk by path_margin metres on every side.  Returns [(vertices [k, 2]
+    float64 world metres, kind)] with kind 0 obstacle, 1 path boundary."""
+    ext_x = (terrain.nx - 1) * terrain.cell
+    ext_y = (terrain.ny - 1) * terrain.cell
+    u = uniform(seed, 41, 6 * n)
+    out = []
+    for q in range(n):
+        cx = terrain.x0 + ext_x * (0.2 + 0.6 * u[6 * q])
+        cy = terrain.y0 + ext_y * (0.3 + 0.4 * u[6 * q + 1])
+        r = 0.6 + 0.9 * u[6 * q + 2]
+        k = 5 + int(5 * u[6 * q + 3]) % 5
+        a0 = 2 * math.pi * u[6 * q + 4]
+        jit = uniform(seed, 42 + q, k)
+        ang = a0 + 2 * math.pi * (np.arange(k) + 0.3 * (jit - 0.5)) / k
+        out.append((np.stack([cx + r * np.cos(ang), cy + r * np.sin(ang)], 1), 0))
+    m = path_margin
+    box = np.array([[terrain.x0 + m, terrain.y0 + m], [terrain.x0 + ext_x - m, terrain.y0 + m],
+                    [terrain.x0 + ext_x - m, terrain.y0 + ext_y - m], [terrain.x0 + m, terrain.y0 + ext_y - m]])
+    out.append((box, 1))
+    return out
+
+
+def workload_est(seed: int = 0, N: int = 1024, H: int = 40, dt: float = 0.05, scaled: bool = False) -> Workload:
+    """The planar model's workloads: the plain (or scaled) configuration on the
+    planar model's level of detail (Gaussian of 1.5 m, Sec. V-B), with the
+    SRB start state reduced to (x, y, psi, v_By, w_Bz, delta, v_Bx)."""
+    if scaled:
+        w = workload_scaled(seed, N=N, H=H, dt=dt, terrain=terrain_scaled(seed, lod_sigma=1.5))
+    else:
+        ter = terrain_plain(seed, lod_sigma=1.5)
+        veh = vehicle_baseline()
+        x0 = settled_state(ter, veh, 5.0, 25.6, 0.0, 8.0)
+        w = Workload("plain", ter, veh, cost_default(45.0, 25.6), x0, candidates(N, H, seed), dt,
+                     n_sub=n_substeps(dt), meta=dict(seed=seed))
+    x0 = w.x0[..., [0, 1, 3, 7, 11, 12, 6]].astype(np.float32)
+    return Workload(f"est-{w.name}", w.terrain, w.vehicle, w.cost, x0, w.ctrl, w.dt, w.n_sub, meta=w.meta)

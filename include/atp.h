@@ -113,13 +113,21 @@ typedef struct {
     float x, y, z, psi, theta, phi, vx, vy, vz, wx, wy, wz, delta;
 } atp_state;
 
+/* terrain flag bits (atp_terrain.flags) */
+enum {
+    ATP_TERRAIN_HAS_COSTMAP = 1   /* the texels' cost channel holds a costmap */
+};
+
 /* A prepared terrain (see atp_terrain_prepare).  texels is a device pointer
- * owned by the caller, nx * ny texels of the given format. */
+ * owned by the caller, nx * ny texels of the given format.  flags is set by
+ * atp_terrain_prepare; without ATP_TERRAIN_HAS_COSTMAP the kernels skip the
+ * cost channel (it is zero). */
 typedef struct {
     const void *texels;
     int nx, ny;
     double cell, x0, y0;      /* node (i, j) is at (x0 + i cell, y0 + j cell) */
     int format;
+    int flags;
 } atp_terrain;
 
 /* Result of a plan, written to device memory. */
@@ -280,6 +288,64 @@ int atp_sample(atp_ctx *ctx, const float *prev_best_dev, int H_prev, int shift, 
  * atan2f(a, b) (CUDA), 1/b (library reciprocal), 1.0f/b (IEEE division).
  * All pointers are device memory of n (a, b) and 8 n (out) floats. */
 int atp_math_check(const float *a_dev, const float *b_dev, int n, float *out_dev, void *stream);
+
+/* ---- The planar model (App. "Extended Single-Track Vehicle Dynamics
+ * Model"): the formulation the paper sets beside the SRB model. ---------- */
+
+/* one EST state: position, yaw, lateral velocity, yaw rate, steering angle,
+ * longitudinal velocity (the paper's order) */
+typedef struct {
+    float x, y, psi, vy, wz, delta, vx;
+} atp_est_state;
+
+/* Plan with the extended single-track model instead of the SRB model: per
+ * Euler step the terrain's normal under the CoM sets pitch and roll (1-2-3
+ * convention, normal ~ (-f_x, -f_y, 1)), the virtual front and rear tires'
+ * normal forces follow from the load-transfer coefficients, their lateral
+ * forces from the sigmoid tire, and the lateral-acceleration constraint
+ * |a_By - g_By| < abar = g e / (2 (h+R)) replaces the ESM: its soft cost
+ * sigma max(0, 1 - margin / eps)^2 with eps = cost->eps_esm if > 0, else
+ * 0.1 abar, and a candidate is feasible when its minimum margin over the
+ * integrated Euler steps is > 0.  The costmap is read at the four wheel
+ * contact points.  Arguments, outputs and results are those of atp_plan,
+ * with 7-component states: x0 (host) or x0_dev float [7][N]; cand_xf_dev
+ * float [7][N]; margins in m/s^2.  Uses Jzz, Lf, Lr, e, hR, C, mu, the
+ * steering limits and g of the vehicle. */
+int atp_plan_est(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                 const atp_terrain *terrain, const atp_est_state *x0, const float *x0_dev,
+                 const float *ctrl_dev, int N, int H, float dt, int n_sub,
+                 atp_plan_out *out_dev, float *best_ctrl_dev, float *best_margin_dev,
+                 float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
+                 float *cand_xf_dev, void *stream);
+
+/* ---- Terrain preprocessing ---------------------------------------------- */
+
+/* Model-specific level of detail (Sec. V-B): out = the heightmap smoothed by a
+ * Gaussian of standard deviation sigma metres (0.3 m for the SRB model, 1.5 m
+ * for the planar model in the paper), cut at r = floor(4 sigma / cell + 1/2)
+ * cells, with the map extended by its nearest border node.  sigma = 0 copies.
+ *   heights_dev, out_dev  float [ny][nx], device (out may equal heights)
+ *   tmp_dev               float [ny][nx], device scratch, aliasing neither
+ * r <= 512 cells, else ATP_ERR_UNSUPPORTED. */
+int atp_lod_smooth(atp_ctx *ctx, const float *heights_dev, int nx, int ny, double cell,
+                   double sigma, float *tmp_dev, float *out_dev, void *stream);
+
+/* Costmap of the distance constraints (Sec. IV-C, IV-D): at every node
+ * (x0 + i cell, y0 + j cell) the sum over perimeters p of
+ * sigma max(0, 1 - sdist_p / eps)^2, where sdist_p is the distance to p's
+ * edges, negative inside an obstacle (kind 0) and outside a path boundary
+ * (kind 1), inside by the even-odd rule.  The paper uses eps = 0.25 m and
+ * sigma = 1e6.  The result is the costmap_dev input of atp_terrain_prepare.
+ *   xy_dev      double [n_vert][2] perimeter vertices in world metres, device
+ *   start       int [n_poly + 1], host: perimeter p is vertices start[p] ..
+ *               start[p+1]-1, start[0] = 0, start[n_poly] = n_vert, each >= 2
+ *   kind        int [n_poly], host: 0 obstacle, 1 path boundary
+ *   cost_dev    float [ny][nx], device
+ *   sdist_dev   float [ny][nx] or NULL: the smallest signed distance
+ * 1 <= n_poly <= 256. */
+int atp_costmap(atp_ctx *ctx, const double *xy_dev, const int *start, const int *kind, int n_poly,
+                int nx, int ny, double cell, double x0, double y0, double eps, double sigma,
+                float *cost_dev, float *sdist_dev, void *stream);
 
 /* Plan without allocating: atp_plan for callers that cannot allocate device
  * memory once running, such as a planner in a hard real-time control loop

@@ -23,12 +23,13 @@ F32X4, BF16X4 = 0, 1
 OPT_COST_FP64 = 1
 OPT_LANES = 2
 FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
+TERRAIN_HAS_COSTMAP = 1
 
 # every symbol include/atp.h declares
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
            "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch",
-           "atp_set_option", "atp_grad")
+           "atp_set_option", "atp_grad", "atp_plan_est", "atp_lod_smooth", "atp_costmap")
 
 
 class Vehicle(C.Structure):
@@ -50,7 +51,11 @@ class State(C.Structure):
 class TerrainC(C.Structure):
     _fields_ = [("texels", C.c_void_p), ("nx", C.c_int), ("ny", C.c_int),
                 ("cell", C.c_double), ("x0", C.c_double), ("y0", C.c_double),
-                ("format", C.c_int)]
+                ("format", C.c_int), ("flags", C.c_int)]
+
+
+class EstState(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("x", "y", "psi", "vy", "wz", "delta", "vx")]
 
 
 class PlanRequest(C.Structure):
@@ -113,9 +118,17 @@ def load(build_if_missing: bool = True):
                                C.c_int, _vp, _vp, _vp]
         L.atp_sample.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_int, C.c_int, _vp, _vp]
+        L.atp_plan_est.argtypes = [_vp, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
+                                   C.POINTER(EstState), _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
+                                   _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.atp_lod_smooth.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, _vp, _vp, _vp]
+        L.atp_costmap.argtypes = [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.c_int,
+                                  C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                  _vp, _vp, _vp]
         for n in ("atp_create", "atp_destroy", "atp_reserve", "atp_terrain_prepare",
                   "atp_plan", "atp_rollout", "atp_plan_noalloc", "atp_math_check", "atp_sample",
-                  "atp_plan_batch", "atp_set_option", "atp_grad"):
+                  "atp_plan_batch", "atp_set_option", "atp_grad", "atp_plan_est", "atp_lod_smooth",
+                  "atp_costmap"):
             getattr(L, n).restype = C.c_int
         _lib = L
         return L
@@ -229,6 +242,66 @@ class Context:
                                _ptr(o.get("xf")), _stream(stream))
         self._check(rc, "atp_plan")
         return o
+
+    def plan_est(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0, out=None,
+                 stream=None, want_candidates=True, want_xf=False):
+        """Plan with the planar EST model (atp_plan_est).  x0: 7 floats (x, y,
+        psi, v_By, w_Bz, delta, v_Bx) or a float32 CUDA tensor [7, N]."""
+        import torch
+        H, N, _ = ctrl.shape
+        dev = ctrl.device
+        o = out if out is not None else {}
+        if "out" not in o:
+            o.update(plan_outputs(N, H, device=dev, candidates=want_candidates))
+            if want_xf:
+                o["xf"] = torch.empty((7, N), dtype=torch.float32, device=dev)
+        if isinstance(x0, torch.Tensor):
+            xs, xdev = None, x0
+        else:
+            xs, xdev = EstState(*[float(v) for v in x0]), None
+        rc = self.lib.atp_plan_est(self.h, C.byref(vehicle(veh)), C.byref(cost(cst)),
+                                   C.byref(terrain.c), C.byref(xs) if xs is not None else None,
+                                   _ptr(xdev), _ptr(ctrl), int(N), int(H), float(dt), int(n_sub),
+                                   _ptr(o["out"]), _ptr(o.get("best_ctrl")), _ptr(o.get("best_margin")),
+                                   _ptr(o.get("cost")), _ptr(o.get("margin")), _ptr(o.get("flags")),
+                                   _ptr(o.get("xf")), _stream(stream))
+        self._check(rc, "atp_plan_est")
+        return o
+
+    def lod_smooth(self, heights, cell, sigma, out=None, stream=None):
+        """Gaussian level of detail of a float32 CUDA heightmap [ny, nx]."""
+        import torch
+        ny, nx = heights.shape
+        tmp = torch.empty_like(heights)
+        o = out if out is not None else torch.empty_like(heights)
+        rc = self.lib.atp_lod_smooth(self.h, _ptr(heights), int(nx), int(ny), float(cell), float(sigma),
+                                     _ptr(tmp), _ptr(o), _stream(stream))
+        self._check(rc, "atp_lod_smooth")
+        if stream is not None:          # the allocator frees tmp in the stream's order
+            tmp.record_stream(stream)
+        return o
+
+    def costmap(self, polys, nx, ny, cell, x0=0.0, y0=0.0, eps=0.25, sigma=1e6, want_sdist=False,
+                device="cuda", stream=None):
+        """Distance-constraint costmap float32 CUDA [ny, nx] (and the smallest
+        signed distance) of perimeters given as a list of (vertices [n, 2],
+        kind) with kind 0 obstacle, 1 path boundary."""
+        import numpy as np
+        import torch
+        xy = np.concatenate([np.asarray(p, np.float64).reshape(-1, 2) for p, _ in polys])
+        start = (C.c_int * (len(polys) + 1))(0, *np.cumsum([len(np.asarray(p).reshape(-1, 2))
+                                                            for p, _ in polys]).tolist())
+        kind = (C.c_int * len(polys))(*[int(k) for _, k in polys])
+        xy_d = torch.as_tensor(xy, device=device)
+        cm = torch.empty((ny, nx), dtype=torch.float32, device=device)
+        sd = torch.empty((ny, nx), dtype=torch.float32, device=device) if want_sdist else None
+        rc = self.lib.atp_costmap(self.h, _ptr(xy_d), start, kind, len(polys), int(nx), int(ny),
+                                  float(cell), float(x0), float(y0), float(eps), float(sigma),
+                                  _ptr(cm), _ptr(sd), _stream(stream))
+        self._check(rc, "atp_costmap")
+        if stream is not None:
+            xy_d.record_stream(stream)
+        return (cm, sd) if want_sdist else cm
 
     def plan_batch(self, requests, stream=None):
         """One launch over a ragged batch of plans.  Each request is a dict

@@ -11,8 +11,10 @@
 
 #include "atp.h"
 #include "adjoint.cuh"
+#include "est_kernel.cuh"
 #include "plan_kernel.cuh"
 #include "sampler.cuh"
+#include "terrain_tools.cuh"
 
 struct atp_ctx {
     int device;
@@ -218,6 +220,10 @@ void derive(const atp_vehicle &v, const atp_cost &c, const atp_terrain &t, atp::
     V.cpb = (float)std::cos(phibar);
     V.spb = (float)std::sin(phibar);
     V.tip = (float)(0.5 * M_PI - phibar);
+    V.Kzzf = (float)Kzzf;
+    V.Kzzr = (float)Kzzr;
+    V.Kzx = (float)(v.M * v.hR / L);
+    V.abar = (float)(v.g * v.e / (2.0 * v.hR));      // M g / (2 K_zy), K_zy = M (h+R) / e
     const double U0 = v.M * v.g * Rbar * (1.0 - std::sin(phibar));
     const double eps = c.eps_esm > 0 ? c.eps_esm : 0.1 * U0;
     atp::Cost &C = p.C;
@@ -237,14 +243,15 @@ void derive(const atp_vehicle &v, const atp_cost &c, const atp_terrain &t, atp::
     T.nbx = (t.nx + 7) / 8;
     T.nx = t.nx;
     T.ny = t.ny;
+    T.has_cm = (t.flags & ATP_TERRAIN_HAS_COSTMAP) != 0;
     T.inv_cell = (float)(1.0 / t.cell);
     split(t.x0, T.x0_hi, T.x0_lo);
     split(t.y0, T.y0_hi, T.y0_lo);
 }
 
 int common_checks(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *ter,
-                  const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int N, int H,
-                  float dt, int n_sub, int *n_sub_out)
+                  const float *x0, int n_state, const float *x0_dev, const float *ctrl_dev, int N,
+                  int H, float dt, int n_sub, int *n_sub_out)
 {
     int rc;
     if ((rc = check_vehicle(ctx, veh)) != ATP_OK) return rc;
@@ -252,9 +259,8 @@ int common_checks(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, co
     if ((rc = check_terrain(ctx, ter)) != ATP_OK) return rc;
     if (!x0 && !x0_dev) return fail(ctx, ATP_ERR_INVALID, "need x0 or x0_dev");
     if (x0) {
-        const float *s = &x0->x;
-        for (int q = 0; q < 13; ++q)
-            if (!std::isfinite(s[q])) return fail(ctx, ATP_ERR_INVALID, "x0 is not finite");
+        for (int q = 0; q < n_state; ++q)
+            if (!std::isfinite(x0[q])) return fail(ctx, ATP_ERR_INVALID, "x0 is not finite");
     }
     if (!ctrl_dev) return fail(ctx, ATP_ERR_INVALID, "ctrl_dev is NULL");
     if ((uintptr_t)ctrl_dev % 8 != 0) return fail(ctx, ATP_ERR_INVALID, "ctrl_dev must be 8-byte aligned");
@@ -410,6 +416,7 @@ int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *cos
         out->x0 = x0;
         out->y0 = y0;
         out->format = format;
+        out->flags = costmap_dev ? ATP_TERRAIN_HAS_COSTMAP : 0;
     }
     return ATP_OK;
 }
@@ -422,7 +429,8 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
 {
     if (!ctx) return ATP_ERR_INVALID;
     int ns = 0;
-    int rc = common_checks(ctx, veh, cost, terrain, x0, x0_dev, ctrl_dev, N, H, dt, n_sub, &ns);
+    int rc = common_checks(ctx, veh, cost, terrain, x0 ? &x0->x : nullptr, 13, x0_dev, ctrl_dev, N, H, dt,
+                           n_sub, &ns);
     if (rc != ATP_OK) return rc;
     if (!out_dev) return fail(ctx, ATP_ERR_INVALID, "out_dev is NULL");
     DeviceGuard g(ctx->device);
@@ -457,7 +465,8 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
 {
     if (!ctx) return ATP_ERR_INVALID;
     int ns = 0;
-    int rc = common_checks(ctx, veh, cost, terrain, x0, x0_dev, ctrl_dev, N, H, dt, n_sub, &ns);
+    int rc = common_checks(ctx, veh, cost, terrain, x0 ? &x0->x : nullptr, 13, x0_dev, ctrl_dev, N, H, dt,
+                           n_sub, &ns);
     if (rc != ATP_OK) return rc;
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
@@ -489,7 +498,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
     int ns[atp::kMaxBatch];
     for (int r = 0; r < n_req; ++r) {
         const atp_plan_request &q = reqs[r];
-        int rc = common_checks(ctx, q.veh, q.cost, q.terrain, q.x0, q.x0_dev, q.ctrl_dev, q.N, q.H,
+        int rc = common_checks(ctx, q.veh, q.cost, q.terrain, q.x0 ? &q.x0->x : nullptr, 13, q.x0_dev,
+                               q.ctrl_dev, q.N, q.H,
                                q.dt, q.n_sub, &ns[r]);
         if (rc != ATP_OK) {
             char why[sizeof ctx->err];
@@ -536,6 +546,124 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
     return ATP_OK;
 }
 
+extern "C" int atp_plan_est(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                            const atp_terrain *terrain, const atp_est_state *x0, const float *x0_dev,
+                            const float *ctrl_dev, int N, int H, float dt, int n_sub,
+                            atp_plan_out *out_dev, float *best_ctrl_dev, float *best_margin_dev,
+                            float *cand_cost_dev, float *cand_margin_dev, uint8_t *cand_flags_dev,
+                            float *cand_xf_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int ns = 0;
+    int rc = common_checks(ctx, veh, cost, terrain, x0 ? &x0->x : nullptr, 7, x0_dev, ctrl_dev, N, H, dt,
+                           n_sub, &ns);
+    if (rc != ATP_OK) return rc;
+    if (!out_dev) return fail(ctx, ATP_ERR_INVALID, "out_dev is NULL");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    if ((rc = ensure_scratch(ctx, N, H)) != ATP_OK) return rc;
+    const RegionLayout L = region_layout((size_t)N, (size_t)H);
+    char *base = (char *)ctx->scratch + kHeaderBytes;
+    atp::PlanParams p;
+    std::memset(&p, 0, sizeof p);
+    derive(*veh, *cost, *terrain, p);
+    // the lateral-acceleration constraint's normaliser (reading Q2)
+    const double abar = veh->g * veh->e / (2.0 * veh->hR);
+    p.C.inv_eps = (float)(1.0 / (cost->eps_esm > 0 ? cost->eps_esm : 0.1 * abar));
+    if (x0) {
+        std::memcpy(p.x0, &x0->x, 7 * sizeof(float));
+        p.x0_soa = nullptr;
+    } else {
+        p.x0_soa = x0_dev;
+    }
+    p.ctrl = (const float2 *)ctrl_dev;
+    p.N = N;
+    p.H = H;
+    p.n_sub = ns;
+    p.h = (float)((double)dt / (double)ns);
+    p.cost = cand_cost_dev ? cand_cost_dev : (float *)(base + L.cost);
+    p.margin = cand_margin_dev ? cand_margin_dev : (float *)(base + L.margin);
+    p.flags = cand_flags_dev ? cand_flags_dev : (uint8_t *)(base + L.flags);
+    p.xf = cand_xf_dev;
+    p.step_margin = (float *)(base + L.step_margin);
+    p.out = out_dev;
+    p.best_ctrl = best_ctrl_dev;
+    p.best_margin = best_margin_dev;
+    p.scratch = (atp::Scratch *)ctx->scratch;
+    p.acc64 = ctx->acc64;
+    cudaError_t e = atp::launch_est(p, true, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "planar plan launch");
+    return ATP_OK;
+}
+
+extern "C" int atp_lod_smooth(atp_ctx *ctx, const float *heights_dev, int nx, int ny, double cell,
+                              double sigma, float *tmp_dev, float *out_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (!heights_dev || !tmp_dev || !out_dev) return fail(ctx, ATP_ERR_INVALID, "a buffer is NULL");
+    if (tmp_dev == heights_dev || tmp_dev == out_dev)
+        return fail(ctx, ATP_ERR_INVALID, "tmp_dev must alias neither heights_dev nor out_dev");
+    if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536)
+        return fail(ctx, ATP_ERR_INVALID, "map must be between 1 and 65536 nodes per side");
+    if (!(cell > 0.0) || !std::isfinite(cell) || !(sigma >= 0.0) || !std::isfinite(sigma))
+        return fail(ctx, ATP_ERR_INVALID, "cell must be > 0 and sigma >= 0, both finite");
+    const double s = sigma / cell;                      // standard deviation in cells
+    const double rr = 4.0 * s + 0.5;
+    if (rr >= (double)atp::kLodMaxRadius + 1.0)
+        return fail(ctx, ATP_ERR_UNSUPPORTED, "Gaussian radius above %d cells", atp::kLodMaxRadius);
+    const int r = sigma > 0.0 ? (int)rr : 0;
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    const float inv2s2 = r > 0 ? (float)(0.5 / (s * s)) : 0.f;
+    cudaError_t e = atp::launch_lod_smooth(heights_dev, tmp_dev, out_dev, nx, ny, r, inv2s2,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "level-of-detail launch");
+    return ATP_OK;
+}
+
+extern "C" int atp_costmap(atp_ctx *ctx, const double *xy_dev, const int *start, const int *kind,
+                           int n_poly, int nx, int ny, double cell, double x0, double y0, double eps,
+                           double sigma, float *cost_dev, float *sdist_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    if (!xy_dev || !start || !kind || !cost_dev) return fail(ctx, ATP_ERR_INVALID, "a buffer is NULL");
+    if (n_poly < 1 || n_poly > atp::kCostmapMaxPolys)
+        return fail(ctx, ATP_ERR_INVALID, "need 1 <= n_poly <= %d", atp::kCostmapMaxPolys);
+    if (start[0] != 0) return fail(ctx, ATP_ERR_INVALID, "start[0] must be 0");
+    for (int q = 0; q < n_poly; ++q) {
+        if (start[q + 1] - start[q] < 2)
+            return fail(ctx, ATP_ERR_INVALID, "perimeter %d has fewer than 2 vertices", q);
+        if (kind[q] != 0 && kind[q] != 1) return fail(ctx, ATP_ERR_INVALID, "kind[%d] must be 0 or 1", q);
+    }
+    if (nx < 1 || ny < 1 || nx > 65536 || ny > 65536)
+        return fail(ctx, ATP_ERR_INVALID, "map must be between 1 and 65536 nodes per side");
+    if (!(cell > 0.0) || !std::isfinite(cell) || !std::isfinite(x0) || !std::isfinite(y0) || !(eps > 0.0) ||
+        !std::isfinite(eps) || !(sigma >= 0.0) || !std::isfinite(sigma))
+        return fail(ctx, ATP_ERR_INVALID, "cell, eps must be > 0, sigma >= 0, all finite");
+    if ((uintptr_t)xy_dev % 8 != 0) return fail(ctx, ATP_ERR_INVALID, "xy_dev must be 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    atp::CostmapParams p;
+    std::memset(&p, 0, sizeof p);
+    p.xy = xy_dev;
+    p.n_poly = n_poly;
+    p.n_vert = start[n_poly];
+    for (int q = 0; q <= n_poly; ++q) p.start[q] = start[q];
+    for (int q = 0; q < n_poly; ++q) p.kind[q] = kind[q];
+    p.nx = nx;
+    p.ny = ny;
+    p.cell = cell;
+    p.x0 = x0;
+    p.y0 = y0;
+    p.inv_eps = (float)(1.0 / eps);
+    p.sigma = (float)sigma;
+    p.cost = cost_dev;
+    p.sdist = sdist_dev;
+    cudaError_t e = atp::launch_costmap(p, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "costmap launch");
+    return ATP_OK;
+}
+
 extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
                         const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
                         const float *ctrl_dev, int K, int H, float dt, int n_sub, int ckpt,
@@ -543,7 +671,8 @@ extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *co
 {
     if (!ctx) return ATP_ERR_INVALID;
     int ns = 0;
-    int rc = common_checks(ctx, veh, cost, terrain, x0, x0_dev, ctrl_dev, K, H, dt, n_sub, &ns);
+    int rc = common_checks(ctx, veh, cost, terrain, x0 ? &x0->x : nullptr, 13, x0_dev, ctrl_dev, K, H, dt,
+                           n_sub, &ns);
     if (rc != ATP_OK) return rc;
     if (terrain->format != ATP_TERRAIN_F32X4)
         return fail(ctx, ATP_ERR_UNSUPPORTED, "the adjoint takes F32X4 terrain only");
@@ -660,7 +789,8 @@ extern "C" int atp_plan_noalloc(const atp_vehicle *veh, const atp_cost *cost,
                                 float *cand_xf_dev, void *stream)
 {
     int ns = 0;
-    int rc = common_checks(nullptr, veh, cost, terrain, x0, x0_dev, ctrl_dev, N, H, dt, n_sub, &ns);
+    int rc = common_checks(nullptr, veh, cost, terrain, x0 ? &x0->x : nullptr, 13, x0_dev, ctrl_dev, N, H, dt,
+                           n_sub, &ns);
     if (rc != ATP_OK) return rc;
     if (!out_dev) return ATP_ERR_INVALID;
     const ScratchLayout L = layout((size_t)N, (size_t)H);

@@ -39,6 +39,9 @@ struct Veh {
     float MgRbar;                    // M g Rbar
     float cpb, spb;                  // cos(phibar), sin(phibar)
     float tip;                       // pi/2 - phibar: roll at which U_ESM = 0
+    // planar (EST) model: load-transfer coefficients and the critical lateral
+    // acceleration M g / (2 K_zy)
+    float Kzzf, Kzzr, Kzx, abar;
 };
 
 struct Cost {
@@ -58,6 +61,7 @@ struct Terrain {
     const float4 *plane16;           // BF16 block planes [ceil(ny/8)][ceil(nx/8)]
     int nbx;                         // blocks per row
     int nx, ny;
+    int has_cm;                      // the texels carry a costmap
     float inv_cell;                  // 1 / cell
     float x0_hi, x0_lo, y0_hi, y0_lo;  // terrain origin
 };

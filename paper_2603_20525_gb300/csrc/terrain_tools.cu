@@ -1,0 +1,237 @@
+// terrain_tools.cu - terrain preprocessing for the planner (arxiv 2603.20525):
+//
+//   * Level of detail (Sec. V-B).  Each model gets its own Gaussian-smoothed
+//     copy of the heightmap (0.3 m standard deviation for the SRB model, the
+//     length scale of a wheel; 1.5 m for the planar model, that of the
+//     chassis).  The two-dimensional Gaussian is a product of one-dimensional
+//     ones, so it runs as a row pass and a column pass, each through a
+//     shared-memory tile with its halo; the map is extended by its nearest
+//     border node and the kernel is cut at four standard deviations.
+//   * Costmap of the distance constraints (Sec. IV-C, IV-D).  At every node
+//     the signed distance to each obstacle or path-boundary perimeter is turned
+//     into the normalised quadratic soft-constraint cost rate and summed over
+//     the perimeters, so that the rollout only interpolates it.  One thread per
+//     node; the perimeters' edges stream through shared memory in chunks.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "terrain_tools.cuh"
+
+namespace atp {
+
+namespace {
+
+constexpr int kRowTile = 256;     // outputs per row-pass CTA
+constexpr int kColTile = 64;      // rows per column-pass CTA (32 columns wide)
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Normalised weights w[k], k = 0..2r, of exp(-(k - r)^2 / (2 s^2)), made by
+// every CTA the same way: the terms, then their sum in a fixed order (per
+// thread a strided run, then a fixed shuffle tree and a fixed pass over the
+// warps), so every CTA holds the same bits.  Needs blockDim.x * blockDim.y a
+// multiple of 32 and at most 1024 threads.
+__device__ void gauss_weights(float *w, int r, float inv2s2)
+{
+    __shared__ float s_part[32];
+    __shared__ float s_total;
+    const int n = 2 * r + 1;
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nt = blockDim.x * blockDim.y;
+    float part = 0.f;
+    for (int k = t; k < n; k += nt) {
+        const float d = (float)(k - r);
+        const float e = expf(-(d * d) * inv2s2);
+        w[k] = e;
+        part += e;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((t & 31) == 0) s_part[t >> 5] = part;
+    __syncthreads();
+    if (t == 0) {
+        float z = 0.f;
+        for (int i = 0; i < nt / 32; ++i) z += s_part[i];
+        s_total = z;
+    }
+    __syncthreads();
+    const float z = s_total;
+    for (int k = t; k < n; k += nt) w[k] = w[k] / z;
+    __syncthreads();
+}
+
+// out[j][i] = sum_k w[k] in[j][clamp(i + k - r)]
+__global__ void __launch_bounds__(kRowTile) lod_rows_kernel(LodParams p)
+{
+    extern __shared__ float sm[];
+    float *w = sm;                           // 2r + 1
+    float *tile = sm + 2 * p.r + 1;          // kRowTile + 2r
+    gauss_weights(w, p.r, p.inv2s2);
+    const int j = blockIdx.y;
+    const int i0 = blockIdx.x * kRowTile;
+    const float *row = p.in + (size_t)j * p.nx;
+    for (int t = threadIdx.x; t < kRowTile + 2 * p.r; t += kRowTile)
+        tile[t] = __ldg(row + clampi(i0 - p.r + t, 0, p.nx - 1));
+    __syncthreads();
+    const int i = i0 + threadIdx.x;
+    if (i >= p.nx) return;
+    float acc = 0.f;
+    for (int k = 0; k <= 2 * p.r; ++k) acc = fmaf(w[k], tile[threadIdx.x + k], acc);
+    p.out[(size_t)j * p.nx + i] = acc;
+}
+
+// out[j][i] = sum_k w[k] in[clamp(j + k - r)][i]; a CTA of 32 x 8 threads
+// covers 32 columns and kColTile rows.
+__global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
+{
+    extern __shared__ float sm[];
+    float *w = sm;                           // 2r + 1, padded to a multiple of 32
+    float *tile = sm + ((2 * p.r + 1 + 31) & ~31);   // [kColTile + 2r][32]
+    gauss_weights(w, p.r, p.inv2s2);
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j0 = blockIdx.y * kColTile;
+    const int ic = min(i, p.nx - 1);
+    for (int t = threadIdx.y; t < kColTile + 2 * p.r; t += 8)
+        tile[t * 32 + threadIdx.x] = __ldg(p.in + (size_t)clampi(j0 - p.r + t, 0, p.ny - 1) * p.nx + ic);
+    __syncthreads();
+    if (i >= p.nx) return;
+    for (int jj = threadIdx.y; jj < kColTile; jj += 8) {
+        const int j = j0 + jj;
+        if (j >= p.ny) break;
+        float acc = 0.f;
+        for (int k = 0; k <= 2 * p.r; ++k) acc = fmaf(w[k], tile[(jj + k) * 32 + threadIdx.x], acc);
+        p.out[(size_t)j * p.nx + i] = acc;
+    }
+}
+
+size_t rows_smem(int r) { return sizeof(float) * (size_t)(2 * r + 1 + kRowTile + 2 * r); }
+size_t cols_smem(int r)
+{
+    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (kColTile + 2 * r) * 32);
+}
+
+}  // namespace
+
+cudaError_t launch_lod_smooth(const float *in, float *tmp, float *out, int nx, int ny, int r,
+                              float inv2s2, cudaStream_t stream)
+{
+    if (r < 0 || r > kLodMaxRadius) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(lod_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rows_smem(kLodMaxRadius));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lod_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cols_smem(kLodMaxRadius));
+    if (e != cudaSuccess) return e;
+    LodParams p;
+    p.nx = nx;
+    p.ny = ny;
+    p.r = r;
+    p.inv2s2 = inv2s2;
+    p.in = in;
+    p.out = tmp;
+    lod_rows_kernel<<<dim3((unsigned)((nx + kRowTile - 1) / kRowTile), (unsigned)ny), kRowTile,
+                      rows_smem(r), stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    p.in = tmp;
+    p.out = out;
+    lod_cols_kernel<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + kColTile - 1) / kColTile)),
+                      dim3(32, 8), cols_smem(r), stream>>>(p);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Costmap.  Coordinates are taken relative to the terrain origin (in FP64 once
+// per vertex and node, then FP32), so that the FP32 distance arithmetic works
+// on metres from the map corner rather than on large world coordinates.
+
+namespace {
+
+constexpr int kChunk = 256;       // vertices staged per pass, one per thread
+
+__device__ __forceinline__ int poly_of(const CostmapParams &p, int v)
+{
+    int lo = 0, hi = p.n_poly;               // start[lo] <= v < start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.start[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) costmap_kernel(const __grid_constant__ CostmapParams p)
+{
+    __shared__ float2 s_a[kChunk], s_b[kChunk];
+    __shared__ int s_poly[kChunk];
+    const int i = blockIdx.x * 16 + threadIdx.x;
+    const int j = blockIdx.y * 16 + threadIdx.y;
+    const int t = threadIdx.y * 16 + threadIdx.x;
+    const bool live = i < p.nx && j < p.ny;
+    const float px = (float)((double)i * p.cell), py = (float)((double)j * p.cell);
+    float c = 0.f, smin = CUDART_INF_F;
+    int cur = -1;
+    float d2 = CUDART_INF_F;
+    bool inside = false;
+    // the signed distance of the polygon just finished and its cost
+    auto finish = [&](int q) {
+        const float d = sqrtf(d2);
+        const bool neg = p.kind[q] == 0 ? inside : !inside;
+        const float s = neg ? -d : d;
+        const float v = 1.f - s * p.inv_eps;
+        if (v > 0.f) c = fmaf(p.sigma * v, v, c);
+        smin = fminf(smin, s);
+    };
+    for (int c0 = 0; c0 < p.n_vert; c0 += kChunk) {
+        __syncthreads();
+        const int v = c0 + t;
+        if (v < p.n_vert) {
+            const int q = poly_of(p, v);
+            const int nxt = v + 1 < p.start[q + 1] ? v + 1 : p.start[q];
+            s_a[t] = make_float2((float)(p.xy[2 * v] - p.x0), (float)(p.xy[2 * v + 1] - p.y0));
+            s_b[t] = make_float2((float)(p.xy[2 * nxt] - p.x0), (float)(p.xy[2 * nxt + 1] - p.y0));
+            s_poly[t] = q;
+        }
+        __syncthreads();
+        const int m = min(kChunk, p.n_vert - c0);
+        for (int e = 0; e < m; ++e) {
+            const int q = s_poly[e];
+            if (q != cur) {
+                if (cur >= 0) finish(cur);
+                cur = q;
+                d2 = CUDART_INF_F;
+                inside = false;
+            }
+            const float2 a = s_a[e], b = s_b[e];
+            // distance to the segment a-b
+            const float ex = b.x - a.x, ey = b.y - a.y;
+            const float rx = px - a.x, ry = py - a.y;
+            const float l2 = fmaf(ex, ex, ey * ey);
+            float u = l2 > 0.f ? fmaf(rx, ex, ry * ey) / l2 : 0.f;
+            u = fminf(fmaxf(u, 0.f), 1.f);
+            const float dx = px - fmaf(u, ex, a.x), dy = py - fmaf(u, ey, a.y);
+            d2 = fminf(d2, fmaf(dx, dx, dy * dy));
+            // even-odd rule, ray towards +x
+            if ((a.y > py) != (b.y > py)) {
+                const float xc = fmaf((py - a.y) / (b.y - a.y), ex, a.x);
+                if (px < xc) inside = !inside;
+            }
+        }
+    }
+    if (cur >= 0) finish(cur);
+    if (!live) return;
+    const size_t o = (size_t)j * p.nx + i;
+    p.cost[o] = c;
+    if (p.sdist) p.sdist[o] = smin;
+}
+
+}  // namespace
+
+cudaError_t launch_costmap(const CostmapParams &p, cudaStream_t stream)
+{
+    const dim3 grid((unsigned)((p.nx + 15) / 16), (unsigned)((p.ny + 15) / 16));
+    costmap_kernel<<<grid, dim3(16, 16), 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace atp

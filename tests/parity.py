@@ -25,6 +25,10 @@ the candidate's conditioning, at least 1e-4 of the preload); U_ESM = 0, which
 decides feasibility; the goal circle.  Infeasible candidates (their roll
 crossed the tipping point of the ESM, beyond which the fall diverges
 exponentially) are compared on their feasibility bit only.
+
+The planar (EST) model is held to the same protocol with its own state
+floors and margin floor (1 % of abar); its feasibility switch is the
+lateral-acceleration margin at 0, and it has no contact switch.
 """
 import math
 
@@ -33,6 +37,8 @@ import numpy as np
 TOL = 1e-4
 KAPPA = 20.0
 STATE_FLOORS = np.array([1.0, 1.0, 1.0, 0.01, 0.01, 0.01, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.01])
+# the planar (EST) model's state: x, y, psi, v_By, w_Bz, delta, v_Bx
+EST_FLOORS = np.array([1.0, 1.0, 0.01, 0.1, 0.1, 0.01, 0.1])
 COST_FLOOR = 1.0
 # distances to a switch (as normalised by the oracle's diag output) below which
 # FP32 and FP64 may take different branches
@@ -47,6 +53,16 @@ TAIL_FACTOR = 4.0       # a capped tail may exceed the bound by this much
 def level_esm(veh):
     Rb = math.hypot(veh["hR"], 0.5 * veh["e"])
     return veh["M"] * veh["g"] * (Rb - veh["hR"])
+
+
+def lateral_bound(veh):
+    """abar = g e / (2 (h + R)), the planar model's critical lateral acceleration."""
+    return veh["g"] * veh["e"] / (2.0 * veh["hR"])
+
+
+def margin_floor(veh, model="srb"):
+    """1 % of the level-ground ESM (SRB) or of abar (EST)."""
+    return 0.01 * (level_esm(veh) if model == "srb" else lateral_bound(veh))
 
 
 def branch_sensitive(diag, sens=None):
@@ -64,15 +80,15 @@ def rel(g, o, floor):
     return np.where(np.isnan(e), np.inf, e)
 
 
-def compare(gpu: dict, orc: dict, veh: dict):
+def compare(gpu: dict, orc: dict, veh: dict, model="srb"):
     """Per-candidate max relative error over cost, margin and final state."""
-    U0 = level_esm(veh)
     eJ = rel(gpu["cost"], orc["J"], COST_FLOOR)
-    eM = rel(gpu["margin"], orc["margin"], 0.01 * U0)
+    eM = rel(gpu["margin"], orc["margin"], margin_floor(veh, model))
     err = np.maximum(eJ, eM)
     eX = None
     if gpu.get("xf") is not None and orc.get("xf") is not None:
-        eX = rel(gpu["xf"], orc["xf"], STATE_FLOORS[None, :])
+        floors = STATE_FLOORS if model == "srb" else EST_FLOORS
+        eX = rel(gpu["xf"], orc["xf"], floors[None, :])
         err = np.maximum(err, eX.max(axis=1))
     return dict(err=err, eJ=eJ, eM=eM, eX=eX)
 
@@ -84,21 +100,22 @@ def nudge(a, rng):
     return np.nextafter(a, np.where(up, np.float32(np.inf), np.float32(-np.inf))).astype(np.float32)
 
 
-def conditioning(oracle, veh, cost, ter, x0, ctrl, dt, n_sub, base, seed=0):
+def conditioning(oracle, veh, cost, ter, x0, ctrl, dt, n_sub, base, seed=0, model="srb"):
     """Largest per-candidate change of the FP64 result over N_NUDGES one-ulp
     nudges of the initial state(s) and the controls."""
     rng = np.random.default_rng(seed)
     sens = np.zeros(len(base["J"]))
+    roll = oracle.rollout if model == "srb" else oracle.est_rollout
     for _ in range(N_NUDGES):
-        r = oracle.rollout(veh, cost, ter, nudge(x0, rng), nudge(ctrl, rng), dt, n_sub)
-        c = compare(dict(cost=r["J"], margin=r["margin"], xf=r["xf"]), base, veh)
+        r = roll(veh, cost, ter, nudge(x0, rng), nudge(ctrl, rng), dt, n_sub)
+        c = compare(dict(cost=r["J"], margin=r["margin"], xf=r["xf"]), base, veh, model)
         sens = np.maximum(sens, c["err"])
     return sens
 
 
-def classify(gpu: dict, orc: dict, sens, veh: dict):
+def classify(gpu: dict, orc: dict, sens, veh: dict, model="srb"):
     """Per-candidate verdict.  Returns a dict of boolean masks and stats."""
-    c = compare(gpu, orc, veh)
+    c = compare(gpu, orc, veh, model)
     err = c["err"]
     feas = (orc["flags"] & 1) > 0
     near = branch_sensitive(orc["diag"], sens)
