@@ -239,6 +239,59 @@ def run_paper_config(ctx, dev, stream, flush, steps=10, warmup=3):
                              "samples/s on an RTX 6000 Ada (Sec. IV-D); other hardware"}
 
 
+def _time(fn, steps, warmup, stream, flush):
+    import torch
+    for _ in range(warmup):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def run_variants(ctx, dev, stream, flush, steps=10):
+    """The other kernels of the library on this GPU: the planar (EST) model on
+    the scaled workload (its own 1.5 m level of detail), and the terrain
+    preprocessing (Gaussian level of detail and the distance-constraint
+    costmap) on a 2048^2 map at 0.1 m."""
+    import gen
+    import torch
+    out = {}
+    w = gen.workload_est(0, N=16384, H=100, dt=0.02, scaled=True)
+    ter = ctx.terrain_prepare(torch.as_tensor(w.terrain.heights).to(dev), w.terrain.cell,
+                              w.terrain.x0, w.terrain.y0)
+    ctrl = torch.as_tensor(w.ctrl).to(dev)
+    x0 = torch.as_tensor(np.ascontiguousarray(w.x0.T)).to(dev)
+    o = ctx.plan_est(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False)
+    ms = _time(lambda: ctx.plan_est(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, out=o),
+               steps, 3, stream, flush)
+    out["est_plan"] = {"workload": f"planar model, {w.N} candidates x H={w.H} at dt={w.dt} s "
+                                   f"({w.n_sub} Euler steps), 1024^2 map, 1.5 m level of detail",
+                       "ms_per_plan": ms, "rollout_steps_per_s": w.N * w.H / (ms / 1e3),
+                       "substeps_per_s": w.N * w.H * w.n_sub / (ms / 1e3)}
+    t = gen.terrain_tile(2048, 5, lod_sigma=0.0)
+    h = torch.as_tensor(t.heights).to(dev)
+    sm = torch.empty_like(h)
+    for sig in (0.3, 1.5):
+        ms = _time(lambda: ctx.lod_smooth(h, t.cell, sig, out=sm), steps, 3, stream, flush)
+        out[f"lod_{sig}m"] = {"workload": f"2048^2 at {t.cell} m, sigma {sig} m "
+                                          f"(radius {int(4 * sig / t.cell + 0.5)} cells)",
+                              "ms": ms, "nodes_per_s": 2048 * 2048 / (ms / 1e3),
+                              "hbm_gbs_min_traffic": 4 * 4 * 2048 * 2048 / (ms / 1e3) / 1e9}
+    polys = gen.obstacles(t, 5, n=24)
+    nv = sum(len(p) for p, _ in polys)
+    ms = _time(lambda: ctx.costmap(polys, t.nx, t.ny, t.cell, t.x0, t.y0), steps, 3, stream, flush)
+    out["costmap"] = {"workload": f"2048^2 nodes, {len(polys)} perimeters, {nv} edges", "ms": ms,
+                      "node_edge_pairs_per_s": 2048 * 2048 * nv / (ms / 1e3)}
+    return out
+
+
 def run_serving(seconds, device):
     """The serving stream: 32 vehicles, each on its own resident 512-2048^2
     tile, Poisson plan requests at 20 Hz per vehicle with N in {1k, 4k, 16k,
@@ -274,6 +327,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scaled", choices=["scaled", "plain", "paper"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="threads per candidate (ATP_OPT_LANES; 0 chooses by batch size)")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="seconds of the 32-vehicle request stream (0: skip)")
     args = ap.parse_args()
@@ -295,6 +350,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     ctx = atp.Context(local)
+    ctx.set_option(atp.OPT_LANES, args.lanes)
     ctx.reserve(w.N, w.H)
     heights = torch.as_tensor(w.terrain.heights).to(dev)
     ter = ctx.terrain_prepare(heights, w.terrain.cell, w.terrain.x0, w.terrain.y0)
@@ -382,7 +438,8 @@ def main():
             "metric": "rollout-steps/s", "value": value, "unit": "rollout-steps/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": workload_config(w, args.workload),
+            "data": "synthetic",
+            "config": dict(workload_config(w, args.workload), threads_per_candidate=ctx.plan_lanes(w.N)),
             "substeps_per_s": value * w.n_sub,
             "latency_ms": {"p50": float(np.percentile(per_step, 50)),
                            "p99": float(np.percentile(per_step, 99))},
@@ -399,6 +456,7 @@ def main():
         }
         if args.workload != "paper":
             line["paper_configuration"] = run_paper_config(ctx, dev, stream, flush)
+            line["other_kernels"] = run_variants(ctx, dev, stream, flush)
         if args.serve_seconds > 0:
             line["serving"] = run_serving(args.serve_seconds, local)
         if not args.no_cpu_baseline and ws == 1:

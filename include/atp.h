@@ -76,7 +76,7 @@ enum {
 enum {
     ATP_OPT_COST_FP64 = 1,    /* accumulate the running cost in FP64 (default 0: FP32) */
     ATP_OPT_LANES = 2         /* threads per candidate in atp_plan / atp_rollout: 0 chooses
-                                 by batch size (default), 1 or 4 forces it */
+                                 by batch size (default), 1, 2 or 4 forces it */
 };
 
 /* per-candidate flag bits */
@@ -170,13 +170,19 @@ size_t atp_terrain_bytes(int nx, int ny, int format);
 /* Set a context option for the calls that follow on this context:
  * ATP_OPT_COST_FP64 (value 0 or 1) accumulates each candidate's running cost
  * (time, control effort and the soft ESM and costmap constraints, Sec. IV-C)
- * in FP64 instead of FP32; ATP_OPT_LANES (0, 1 or 4) sets the threads per
- * candidate of atp_plan and atp_rollout (four split the wheels: lower latency
- * for small batches; one: more throughput once a batch fills the GPU).  The
- * choice changes the summation order of the wheel forces, so results differ
- * in the last bits between 1 and 4 lanes.  Returns ATP_ERR_INVALID for an
- * unknown option or value. */
+ * in FP64 instead of FP32; ATP_OPT_LANES (0, 1, 2 or 4) sets the threads per
+ * candidate of atp_plan and atp_rollout (two split the axles and four the
+ * wheels: lower latency for small batches; one: more throughput once a batch
+ * fills the GPU).  One and two lanes give the same bits; four sum the wheel
+ * forces in another order, so their results differ in the last bits.
+ * Returns ATP_ERR_INVALID for an unknown option or value. */
 int atp_set_option(atp_ctx *ctx, int option, int value);
+
+/* Threads per candidate (1, 2 or 4) that atp_plan and atp_rollout on this
+ * context use for a plan of N candidates: the ATP_OPT_LANES value if set,
+ * else the library's choice by batch size.  Returns ATP_ERR_INVALID for a
+ * NULL context or N < 1. */
+int atp_plan_lanes(const atp_ctx *ctx, int N);
 
 /* Build the texels of a terrain: per node the height, its slope f_x, f_y by
  * central differences (one-sided on the border) and the optional costmap

@@ -18,7 +18,10 @@
  *       with each integrated Euler step (it needs the held control); frozen
  *       states after the goal and the final state add nothing; a candidate is
  *       feasible when its minimum margin is > 0 and its rollout finite;
- *   Q2  eps of the constraint defaults to 10 % of abar = M g / (2 K_zy).
+ *   Q2  eps of the constraint defaults to 10 % of abar = M g / (2 K_zy);
+ *   Q17 the planar model reads the terrain under the CoM only, and the
+ *       costmap under the four wheels when a costmap is given; the off-map
+ *       flag covers the reads that happen.
  */
 #include <math.h>
 #include <string.h>
@@ -115,9 +118,10 @@ static int est_derivative(const orc_vehicle *v, const est_consts *k, const orc_c
     const double viol = 1.0 - margin / k->eps;          /* 1 + pi / eps, pi = -margin */
     double L = c->wt + c->wc * zeta[0] * zeta[0];
     if (viol > 0.0) L += c->sigma * viol * viol;
-    /* distance constraints: the costmap under each wheel */
-    double cm[4];
-    for (int i = 0; i < 4; ++i) {
+    /* distance constraints: the costmap under each wheel (reading Q17: read
+     * only when there is a costmap) */
+    double cm[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < 4 && t->costmap; ++i) {
         const double px = xi[EX] + R[0] * k->rho[i][0] + R[1] * k->rho[i][1] + R[2] * k->rho[i][2];
         const double py = xi[EY] + R[3] * k->rho[i][0] + R[4] * k->rho[i][1] + R[5] * k->rho[i][2];
         double w[4];

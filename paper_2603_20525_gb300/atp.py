@@ -29,7 +29,8 @@ TERRAIN_HAS_COSTMAP = 1
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
            "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch",
-           "atp_set_option", "atp_grad", "atp_plan_est", "atp_lod_smooth", "atp_costmap")
+           "atp_set_option", "atp_grad", "atp_plan_est", "atp_lod_smooth", "atp_costmap",
+           "atp_plan_lanes")
 
 
 class Vehicle(C.Structure):
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True):
                                C.c_int, _vp, _vp, _vp]
         L.atp_sample.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_int, C.c_int, _vp, _vp]
+        L.atp_plan_lanes.argtypes = [_vp, C.c_int]
+        L.atp_plan_lanes.restype = C.c_int
         L.atp_plan_est.argtypes = [_vp, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
                                    C.POINTER(EstState), _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                                    _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -197,6 +200,12 @@ class Context:
 
     def set_option(self, option: int, value: int):
         self._check(self.lib.atp_set_option(self.h, int(option), int(value)), "atp_set_option")
+
+    def plan_lanes(self, N: int) -> int:
+        """Threads per candidate a plan of N candidates runs with."""
+        rc = self.lib.atp_plan_lanes(self.h, int(N))
+        self._check(rc if rc < 0 else ATP_OK, "atp_plan_lanes")
+        return rc
 
     def reserve(self, N: int, H: int):
         self._check(self.lib.atp_reserve(self.h, int(N), int(H)), "atp_reserve")

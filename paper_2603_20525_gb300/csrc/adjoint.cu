@@ -93,7 +93,7 @@ __device__ __forceinline__ void wheel_fwd(const Veh &V, const Terrain &T, const 
     w.t10 = __ldg(r0 + 1);
     w.t01 = __ldg(r0 + T.nx);
     w.t11 = __ldg(r0 + T.nx + 1);
-    w.t = lerp4(w.t00, w.t10, w.t01, w.t11, w.a, w.b);
+    w.t = lerp4(w.t00, w.t10, w.t01, w.t11, w.a, w.b, T.has_cm != 0);
     w.tx = fmaf(-R[3], w.t.z, fmaf(-R[0], w.t.y, R[6]));
     w.ty = fmaf(-R[4], w.t.z, fmaf(-R[1], w.t.y, R[7]));
     w.tz = fmaf(-R[5], w.t.z, fmaf(-R[2], w.t.y, R[8]));

@@ -375,8 +375,8 @@ int atp_set_option(atp_ctx *ctx, int option, int value)
         return ATP_OK;
     }
     if (option == ATP_OPT_LANES) {
-        if (value != 0 && value != 1 && value != 4)
-            return fail(ctx, ATP_ERR_INVALID, "ATP_OPT_LANES takes 0, 1 or 4");
+        if (value != 0 && value != 1 && value != 2 && value != 4)
+            return fail(ctx, ATP_ERR_INVALID, "ATP_OPT_LANES takes 0, 1, 2 or 4");
         ctx->lanes = value;
         return ATP_OK;
     }
@@ -488,6 +488,12 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
 
 }  // extern "C"
 
+extern "C" int atp_plan_lanes(const atp_ctx *ctx, int N)
+{
+    if (!ctx || N < 1) return ATP_ERR_INVALID;
+    return atp::plan_lanes(ctx->lanes, N);
+}
+
 extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *stream)
 {
     if (!ctx) return ATP_ERR_INVALID;
@@ -509,7 +515,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
         if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
         need += region_layout((size_t)q.N, (size_t)q.H).total;
-        ctas += ((long long)q.N * atp::plan_lanes(ctx->lanes, q.N) + atp::kPlanBlock - 1) / atp::kPlanBlock;
+        ctas += ((long long)q.N * (atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1) + atp::kPlanBlock - 1) /
+                atp::kPlanBlock;
     }
     if (ctas > 0x7fffffffLL) return fail(ctx, ATP_ERR_UNSUPPORTED, "batch too large");
     DeviceGuard g(ctx->device);
@@ -537,7 +544,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         p.best_margin = q.best_margin_dev;
         p.scratch = (atp::Scratch *)ctx->scratch + r;
         p.acc64 = ctx->acc64;
-        p.lanes = atp::plan_lanes(ctx->lanes, q.N);
+        // two lanes give the same bits as one, so a batch runs them as one
+        p.lanes = atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1;
         region += L.total;
         b.cta_begin[r + 1] = b.cta_begin[r] + (int)(((long long)q.N * p.lanes + atp::kPlanBlock - 1) / atp::kPlanBlock);
     }

@@ -5,7 +5,7 @@
 //
 // One thread per candidate (the model has 7 states and one terrain lookup
 // under the CoM per Euler step, plus four costmap lookups at the wheels when
-// the terrain carries a costmap).  Pitch and roll are not states: they follow
+// the terrain carries a costmap, reading Q17).  Pitch and roll are not states: they follow
 // the terrain's normal under the CoM, whose components give their sines and
 // cosines directly (1-2-3 convention), so the step needs two trigonometric
 // evaluations (yaw and steering) and two arctangents (the virtual tires'
@@ -26,12 +26,11 @@ namespace {
 // the texels' cost channel; sets `off` for a query outside the map.
 template <int TEX>
 __device__ __forceinline__ float cost_at(const Terrain &T, int icx, float fcx, int icy, float fcy, float ox,
-                                         float oy, bool load, bool &off)
+                                         float oy, bool &off)
 {
     float a, b;
     const int i = axis(icx, fcx, ox, T.inv_cell, T.nx, a, off);
     const int j = axis(icy, fcy, oy, T.inv_cell, T.ny, b, off);
-    if (!load) return 0.f;
     return bilerp<TEX>(T, i, j, a, b).w;
 }
 
@@ -128,16 +127,17 @@ __device__ __forceinline__ void est_one(const PlanParams &p, int j, float &J, fl
             const float m = V.abar - fabsf(aBy - gBy);
             margin = fminf(margin, m);
             sm = fminf(sm, m);
-            // distance constraints: the costmap at the four contact points
+            // distance constraints: the costmap at the four contact points,
+            // read only when the terrain has one (reading Q17)
             float csum = 0.f;
-            {
+            if (cm) {
                 const float ofx = fmaf(R02, -V.hR, R00 * V.Lf), ofy = fmaf(R12, -V.hR, R10 * V.Lf);
                 const float orx = fmaf(R02, -V.hR, -R00 * V.Lr), ory = fmaf(R12, -V.hR, -R10 * V.Lr);
                 const float lx = R01 * V.he, ly = R11 * V.he;
-                const float cfl = cost_at<TEX>(T, icx, fcx, icy, fcy, ofx + lx, ofy + ly, cm, off);
-                const float cfr = cost_at<TEX>(T, icx, fcx, icy, fcy, ofx - lx, ofy - ly, cm, off);
-                const float crl = cost_at<TEX>(T, icx, fcx, icy, fcy, orx + lx, ory + ly, cm, off);
-                const float crr = cost_at<TEX>(T, icx, fcx, icy, fcy, orx - lx, ory - ly, cm, off);
+                const float cfl = cost_at<TEX>(T, icx, fcx, icy, fcy, ofx + lx, ofy + ly, off);
+                const float cfr = cost_at<TEX>(T, icx, fcx, icy, fcy, ofx - lx, ofy - ly, off);
+                const float crl = cost_at<TEX>(T, icx, fcx, icy, fcy, orx + lx, ory + ly, off);
+                const float crr = cost_at<TEX>(T, icx, fcx, icy, fcy, orx - lx, ory - ly, off);
                 csum = (cfl + cfr) + (crl + crr);
             }
             const float soft = fmaxf(fmaf(-m, Cc.inv_eps, 1.f), 0.f);

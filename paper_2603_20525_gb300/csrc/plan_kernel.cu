@@ -30,11 +30,20 @@ __device__ __forceinline__ float quad_sum(float v, unsigned mask)
     return v;
 }
 
+// Sum of v over the two lanes of a candidate's pair (a0 + a1 in both).
+__device__ __forceinline__ float pair_sum(float v, unsigned mask)
+{
+    return v + __shfl_xor_sync(mask, v, 1);
+}
+
 // One candidate per LANES consecutive threads.  LANES = 1: a thread runs all
-// four wheels.  LANES = 4: lane q of the quad runs wheel q (fl, fr, rl, rr)
-// and the body-level arithmetic is repeated bit-identically on all four, so
-// the quad never needs to exchange state, only the five force/moment sums
-// and the costmap sum (two shuffles each).
+// four wheels.  LANES = 2: lane 0 runs the front axle's two wheels, lane 1
+// the rear's; each sums its axle, then one xor-shuffle per sum gives both
+// the same totals, in the same order as one lane computes them, so one and
+// two lanes give the same bits.  LANES = 4: lane q of the quad runs wheel q
+// (fl, fr, rl, rr).  The body-level arithmetic is repeated bit-identically on
+// every lane of a candidate, so lanes never exchange state, only the five
+// force/moment sums and the costmap sum.
 template <int LANES, bool PER_X0, int TEX>
 __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, unsigned qmask,
                                             float &J, float &margin, bool &feasible)
@@ -43,8 +52,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
     const Cost &Cc = p.C;
     const Terrain &T = p.T;
     {
-        // this lane's wheel (LANES = 4)
-        const bool front = q < 2;
+        // this lane's wheel (LANES = 4) or axle (LANES = 2)
+        const bool front = LANES == 2 ? q == 0 : q < 2;
         const float wrx = front ? V.Lf : -V.Lr;
         const float wry = (q & 1) ? -V.he : V.he;
         const float wk = front ? V.kf : V.kr;
@@ -139,9 +148,21 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     FyB = Fyf + Fyr;
                     FzB = (fl.Fz + fr.Fz) + (rl.Fz + rr.Fz);
                     Mx = fmaf(V.hR, FyB, V.he * ((fl.Fz - fr.Fz) + (rl.Fz - rr.Fz)));
-                    My = fmaf(V.Lr, rl.Fz + rr.Fz, -V.Lf * (fl.Fz + fr.Fz));
-                    Mz = fmaf(V.Lf, Fyf, -V.Lr * Fyr);
+                    My = -V.Lf * (fl.Fz + fr.Fz) + V.Lr * (rl.Fz + rr.Fz);
+                    Mz = V.Lf * Fyf + -V.Lr * Fyr;
                     csum = (fl.cost + fr.cost) + (rl.cost + rr.cost);
+                } else if (LANES == 2) {
+                    // this lane's axle: left and right wheel
+                    const WheelOut l = wheel<TEX>(V, T, B, wrx, V.he, wk, wb, wFs, front ? d : 0.f, off);
+                    const WheelOut r = wheel<TEX>(V, T, B, wrx, -V.he, wk, wb, wFs, front ? d : 0.f, off);
+                    const float fy = front ? (l.Fy + r.Fy) * cd : l.Fy + r.Fy;
+                    const float fz = l.Fz + r.Fz;
+                    FyB = pair_sum(fy, qmask);
+                    FzB = pair_sum(fz, qmask);
+                    Mx = fmaf(V.hR, FyB, V.he * pair_sum(l.Fz - r.Fz, qmask));
+                    My = pair_sum(-wrx * fz, qmask);
+                    Mz = pair_sum(wrx * fy, qmask);
+                    csum = T.has_cm ? pair_sum(l.cost + r.cost, qmask) : 0.f;
                 } else {
                     const WheelOut w = wheel<TEX>(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, off);
                     const float fy = front ? w.Fy * cd : w.Fy;
@@ -150,7 +171,7 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     Mx = fmaf(V.hR, FyB, quad_sum(wry * w.Fz, qmask));
                     My = quad_sum(-wrx * w.Fz, qmask);
                     Mz = quad_sum(wrx * fy, qmask);
-                    csum = quad_sum(w.cost, qmask);
+                    csum = T.has_cm ? quad_sum(w.cost, qmask) : 0.f;
                 }
                 const float Fx = V.halfM * fmaf(-wz, vy, fmaf(wy, vz, ax - gBx));
                 My = fmaf(-V.hR, 2.f * Fx, My);
@@ -190,8 +211,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
             }
             if (p.step_margin && q == 0) p.step_margin[(size_t)k * p.N + j] = sm;
         }
-        if (LANES == 4) {
-            // the off-map flag is per wheel: OR it over the quad
+        if (LANES > 1) {
+            // the off-map flag is per wheel: OR it over the candidate's lanes
             off = __any_sync(qmask, off);
         }
         // final state: margin, goal test, terminal cost Phi (Sec. IV-C)
@@ -245,7 +266,8 @@ plan_kernel(const __grid_constant__ PlanParams p)
     const int j = tid / LANES;
     const int q = LANES == 1 ? 0 : (tid & (LANES - 1));
     const bool live = j < p.N;
-    const unsigned qmask = LANES == 1 ? 0u : (0xfu << (threadIdx.x & 28));
+    const unsigned qmask = LANES == 1 ? 0u : LANES == 2 ? (0x3u << (threadIdx.x & 30))
+                                                        : (0xfu << (threadIdx.x & 28));
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
     if (live) rollout_one<LANES, PER_X0, TEX>(p, j, q, qmask, J, margin, feasible);
@@ -325,13 +347,18 @@ static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t s
 
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
 {
-    // four lanes per candidate while the batch leaves the GPU's thread slots
-    // mostly empty (the rollout is then latency bound); one lane once the
-    // batch fills the machine
-    const bool four = plan_lanes(p.lanes, p.N) == 4;
-    if (p.tex_format == TEX_F32)
-        return four ? launch_lanes<4, TEX_F32>(p, reduce, stream) : launch_lanes<1, TEX_F32>(p, reduce, stream);
-    return four ? launch_lanes<4, TEX_BF16>(p, reduce, stream) : launch_lanes<1, TEX_BF16>(p, reduce, stream);
+    // several lanes per candidate while the batch leaves the GPU's thread
+    // slots mostly empty (the rollout is then latency bound); one lane once
+    // the batch fills the machine
+    const int lanes = plan_lanes(p.lanes, p.N);
+    if (p.tex_format == TEX_F32) {
+        if (lanes == 4) return launch_lanes<4, TEX_F32>(p, reduce, stream);
+        if (lanes == 2) return launch_lanes<2, TEX_F32>(p, reduce, stream);
+        return launch_lanes<1, TEX_F32>(p, reduce, stream);
+    }
+    if (lanes == 4) return launch_lanes<4, TEX_BF16>(p, reduce, stream);
+    if (lanes == 2) return launch_lanes<2, TEX_BF16>(p, reduce, stream);
+    return launch_lanes<1, TEX_BF16>(p, reduce, stream);
 }
 
 // Terrain texels (Sec. III-A numeric slope, reading Q10): height, central-

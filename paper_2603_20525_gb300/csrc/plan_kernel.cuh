@@ -44,12 +44,19 @@ struct PlanParams {
 };
 
 constexpr int kPlanBlock = 64;
-// largest batch that runs four lanes (one wheel each) per candidate; above
-// it one lane per candidate gives more rollouts per second on a 152-SM GPU
-constexpr int kLanes4MaxN = 1 << 14;
+// Threads per candidate by batch size, from a sweep of the three layouts on
+// a GB300 (scaled workload, H = 100, 4 Euler steps per control step): four
+// lanes (one wheel each) are fastest up to 16384 candidates (at 16384 by 2 %
+// over two when L2 starts cold), two (one axle each) at 24576, one from
+// 32768 on.
+constexpr int kLanes4MaxN = 16384;
+constexpr int kLanes2MaxN = 28672;
 
-// threads per candidate: `forced` (1 or 4) if set, else by batch size
-inline int plan_lanes(int forced, int N) { return forced ? forced : (N <= kLanes4MaxN ? 4 : 1); }
+// threads per candidate: `forced` (1, 2 or 4) if set, else by batch size
+inline int plan_lanes(int forced, int N)
+{
+    return forced ? forced : (N <= kLanes4MaxN ? 4 : N <= kLanes2MaxN ? 2 : 1);
+}
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream);
 
 // A ragged batch of plans in one launch.  The descriptors travel in the

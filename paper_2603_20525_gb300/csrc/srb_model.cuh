@@ -126,14 +126,21 @@ __device__ __forceinline__ int axis(int ic, float fc, float o, float inv_cell, i
     return i;
 }
 
-__device__ __forceinline__ float4 lerp4(float4 t00, float4 t10, float4 t01, float4 t11, float a, float b)
+__device__ __forceinline__ float lerp2d(float t00, float t10, float t01, float t11, float a, float b)
+{
+    const float lo = fmaf(a, t10 - t00, t00), hi = fmaf(a, t11 - t01, t01);
+    return fmaf(b, hi - lo, lo);
+}
+
+// bilinear height, slopes and (when the terrain has a costmap) cost
+__device__ __forceinline__ float4 lerp4(float4 t00, float4 t10, float4 t01, float4 t11, float a, float b,
+                                        bool cm)
 {
     float4 o;
-    float lo, hi;
-    lo = fmaf(a, t10.x - t00.x, t00.x); hi = fmaf(a, t11.x - t01.x, t01.x); o.x = fmaf(b, hi - lo, lo);
-    lo = fmaf(a, t10.y - t00.y, t00.y); hi = fmaf(a, t11.y - t01.y, t01.y); o.y = fmaf(b, hi - lo, lo);
-    lo = fmaf(a, t10.z - t00.z, t00.z); hi = fmaf(a, t11.z - t01.z, t01.z); o.z = fmaf(b, hi - lo, lo);
-    lo = fmaf(a, t10.w - t00.w, t00.w); hi = fmaf(a, t11.w - t01.w, t01.w); o.w = fmaf(b, hi - lo, lo);
+    o.x = lerp2d(t00.x, t10.x, t01.x, t11.x, a, b);
+    o.y = lerp2d(t00.y, t10.y, t01.y, t11.y, a, b);
+    o.z = lerp2d(t00.z, t10.z, t01.z, t11.z, a, b);
+    o.w = cm ? lerp2d(t00.w, t10.w, t01.w, t11.w, a, b) : 0.f;
     return o;
 }
 
@@ -160,12 +167,13 @@ __device__ __forceinline__ float4 texel16(const Terrain &T, int i, int j)
 template <int TEX>
 __device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a, float b)
 {
+    const bool cm = T.has_cm != 0;
     if (TEX == TEX_F32) {
         const float4 *r0 = T.tex + (size_t)j * T.nx + i;
-        return lerp4(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + T.nx), __ldg(r0 + T.nx + 1), a, b);
+        return lerp4(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + T.nx), __ldg(r0 + T.nx + 1), a, b, cm);
     } else {
         return lerp4(texel16(T, i, j), texel16(T, i + 1, j), texel16(T, i, j + 1),
-                     texel16(T, i + 1, j + 1), a, b);
+                     texel16(T, i + 1, j + 1), a, b, cm);
     }
 }
 

@@ -147,10 +147,11 @@ def test_scaled_plan_parity(ctx):
     assert s["strict_frac"] >= 0.5
 
 
-@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4])
 def test_lanes_option_parity(ctx, lanes):
-    """Both thread layouts, forced: one thread per candidate, and a quad of
-    four threads with one wheel each, on both workloads and a ragged size."""
+    """Every thread layout, forced: one thread per candidate, a pair with one
+    axle each, a quad with one wheel each, on both workloads and a ragged
+    size."""
     from paper_2603_20525_gb300 import atp
     ctx.set_option(atp.OPT_LANES, lanes)
     try:
@@ -159,7 +160,22 @@ def test_lanes_option_parity(ctx, lanes):
     finally:
         ctx.set_option(atp.OPT_LANES, 0)
     with pytest.raises(atp.AtpError, match="INVALID"):
-        ctx.set_option(atp.OPT_LANES, 2)
+        ctx.set_option(atp.OPT_LANES, 3)
+
+
+def test_one_and_two_lanes_same_bits(ctx):
+    """A pair of lanes sums each axle and then the two axles, the order one
+    lane uses, so the two layouts agree bit for bit."""
+    from paper_2603_20525_gb300 import atp
+    w = gen.workload_scaled(3, N=3000, H=30)
+    outs = []
+    for lanes in (1, 2):
+        ctx.set_option(atp.OPT_LANES, lanes)
+        outs.append(gpu_plan(ctx, w))
+    ctx.set_option(atp.OPT_LANES, 0)
+    for k in ("cost", "margin", "flags", "xf", "best_ctrl", "best_margin"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    assert outs[0]["best_idx"] == outs[1]["best_idx"]
 
 
 def test_paper_configuration_sampled(ctx):
