@@ -109,7 +109,7 @@ __device__ __forceinline__ void wheel_fwd(const Veh &V, const Terrain &T, const 
     w.Fz = w.Fk > 0.f ? fmaxf(w.Fb0, 0.f) : 0.f;
     w.alpha = atan2_r(w.viy, w.vix) - di;
     w.Ca = V.C * w.alpha;
-    const float is = rsqrtf(fmaf(w.Ca, w.Ca, V.mu2));
+    const float is = rsq(fmaf(w.Ca, w.Ca, V.mu2));
     w.T = (-w.Ca * V.mu) * is;                    // F_y / F_z
     w.Fy = w.Fz * w.T;
 }
@@ -129,7 +129,7 @@ __device__ __forceinline__ void wheel_adj(const Veh &V, const Terrain &T, const 
     // tire: Fy = Fz T(Ca), T = -mu Ca / sqrt(mu^2 + Ca^2), T' = -mu^3 / (mu^2 + Ca^2)^(3/2)
     aFz += aFy * w.T;
     const float den = fmaf(w.Ca, w.Ca, V.mu2);
-    const float is = rsqrtf(den);
+    const float is = rsq(den);
     const float dT = -V.mu * V.mu2 * is * is * is;
     const float aAlpha = aFy * w.Fz * dT * V.C;
     // alpha = atan2(viy, vix) - di

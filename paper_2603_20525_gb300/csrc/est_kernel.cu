@@ -37,7 +37,7 @@ __device__ __forceinline__ float cost_at(const Terrain &T, int icx, float fcx, i
 __device__ __forceinline__ float tire(const Veh &V, float Fz, float alpha)
 {
     const float Ca = V.C * alpha;
-    return Fz * (-Ca * V.mu) * rsqrtf(fmaf(Ca, Ca, V.mu2));
+    return Fz * (-Ca * V.mu) * rsq(fmaf(Ca, Ca, V.mu2));
 }
 
 template <bool PER_X0, int TEX>
@@ -90,7 +90,7 @@ __device__ __forceinline__ void est_one(const PlanParams &p, int j, float &J, fl
             const int ti = axis(icx, fcx, 0.f, T.inv_cell, T.nx, a, off);
             const int tj = axis(icy, fcy, 0.f, T.inv_cell, T.ny, b, off);
             const float4 t = bilerp<TEX>(T, ti, tj, a, b);
-            const float rn = rsqrtf(fmaf(t.y, t.y, fmaf(t.z, t.z, 1.f)));
+            const float rn = rsq(fmaf(t.y, t.y, fmaf(t.z, t.z, 1.f)));
             const float tx = -t.y * rn, ty = -t.z * rn, tz = rn;
             // 1-2-3 angles of the plane: sin(theta) = tau_x, cos(theta) =
             // |(tau_y, tau_z)|, sin(phi) = -tau_y / cos(theta), cos(phi) = tau_z / cos(theta)

@@ -8,11 +8,24 @@
 
 namespace atp {
 
-// Single MUFU reciprocal (rcp.approx.f32, max error 1 ulp).
+// Single MUFU reciprocal (rcp.approx.ftz.f32, max error 1 ulp).  The .ftz
+// form is one instruction; the form that handles subnormal inputs adds a
+// fix-up sequence.  Every reciprocal of the rollout takes an O(1) quantity
+// (cos theta, the normal's vertical component, a slip ratio's larger side),
+// never a subnormal.
 __device__ __forceinline__ float rcp(float x)
 {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Single MUFU reciprocal square root (rsqrt.approx.ftz.f32), for the tire's
+// mu^2 + (C alpha)^2 >= mu^2 and the unit normal's 1 + |grad f|^2 >= 1.
+__device__ __forceinline__ float rsq(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 

@@ -15,7 +15,7 @@ __global__ void math_check_kernel(const float *__restrict__ a, const float *__re
     float s, c, s_ref, c_ref;
     sincos_r(x, s, c);
     sincosf(x, &s_ref, &c_ref);
-    float *o = out + (size_t)8 * i;
+    float *o = out + (size_t)10 * i;
     o[0] = s;
     o[1] = c;
     o[2] = s_ref;
@@ -24,6 +24,8 @@ __global__ void math_check_kernel(const float *__restrict__ a, const float *__re
     o[5] = atan2f(x, y);
     o[6] = rcp(y);
     o[7] = 1.0f / y;
+    o[8] = rsq(y);
+    o[9] = rsqrtf(y);
 }
 
 }  // namespace atp

@@ -11,7 +11,8 @@
 // of each expression is fixed by the source and the same in every kernel that
 // inlines it.  The slowly varying, large-magnitude
 // state components (position, heading and linear velocity) are accumulated as
-// unevaluated sums hi + lo of two floats (Knuth's TwoSum), and positions are
+// unevaluated sums hi + lo of two floats (Dekker's Fast2Sum per step, Knuth's
+// TwoSum where the start is taken into the terrain frame), and positions are
 // kept relative to the terrain origin and split into an integer cell and a
 // fraction before the lookup.  Without that, the rounding of a 20-100 m
 // coordinate (1e-6 m per Euler step) walks the wheels across the terrain by
@@ -74,11 +75,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// hi + lo += d, renormalised.
+// hi + lo += d: Dekker's Fast2Sum, exact while |hi| >= |d|, which holds for
+// a state component and its increment over one Euler step except near the
+// component's zero, where the plain FP32 sum it then reduces to is accurate
+// to the component's own small magnitude.  Three operations instead of
+// TwoSum's six.
 __device__ __forceinline__ void acc2(float &hi, float &lo, float d)
 {
-    float s, e;
-    two_sum(hi, d, s, e);
+    const float s = __fadd_rn(hi, d);
+    const float e = __fsub_rn(d, __fsub_rn(s, hi));
     hi = s;
     lo = __fadd_rn(lo, e);
 }
@@ -228,7 +233,7 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     const float Fz = Fk > 0.f ? fmaxf(fmaf(-b, chid, Fk), 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
     const float alpha = atan2_r(viy, vix) - di;
     const float Ca = V.C * alpha;
-    const float Fy = Fz * (-Ca * V.mu) * rsqrtf(fmaf(Ca, Ca, V.mu2));
+    const float Fy = Fz * (-Ca * V.mu) * rsq(fmaf(Ca, Ca, V.mu2));
     WheelOut w;
     w.Fz = Fz;
     w.Fy = Fy;

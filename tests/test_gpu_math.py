@@ -1,6 +1,7 @@
 """The rollout's own FP32 elementary functions (sin/cos by Cody-Waite
 reduction and Taylor series, atan2 by octant reduction and a fitted
-polynomial, the MUFU reciprocal) against CUDA's library functions and an
+polynomial, the MUFU reciprocal and reciprocal square root) against CUDA's
+library functions and an
 FP64 reference, on the GPU through atp_math_check."""
 import ctypes as C
 
@@ -16,7 +17,7 @@ def run(a, b):
     L = atp.load()
     ad = torch.as_tensor(np.asarray(a, np.float32)).cuda()
     bd = torch.as_tensor(np.asarray(b, np.float32)).cuda()
-    out = torch.empty((len(a), 8), dtype=torch.float32, device="cuda")
+    out = torch.empty((len(a), 10), dtype=torch.float32, device="cuda")
     assert L.atp_math_check(C.c_void_p(ad.data_ptr()), C.c_void_p(bd.data_ptr()), len(a),
                             C.c_void_p(out.data_ptr()), None) == 0
     torch.cuda.synchronize()
@@ -70,3 +71,15 @@ def test_reciprocal_within_one_ulp():
     rel = np.abs(o[:, 6] - ref) / np.abs(ref)
     assert rel.max() <= 1.2e-7
     assert np.array_equal(o[:, 7], (np.float32(1.0) / b).astype(np.float64))
+
+
+def test_reciprocal_sqrt_within_two_ulp():
+    rng = np.random.default_rng(3)
+    b = np.concatenate([rng.uniform(0.36, 40.0, 200000), 10.0 ** rng.uniform(-30, 30, 100000),
+                        [1.0, 4.0, 0.36]]).astype(np.float32)
+    o = run(np.zeros_like(b), b)
+    ref = 1.0 / np.sqrt(b.astype(np.float64))
+    rel = np.abs(o[:, 8] - ref) / ref
+    rel_cuda = np.abs(o[:, 9] - ref) / ref
+    print("rsqrt max rel error: library", rel.max(), "CUDA", rel_cuda.max())
+    assert rel.max() <= 2.4e-7
