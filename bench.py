@@ -289,6 +289,20 @@ def run_variants(ctx, dev, stream, flush, steps=10):
     ms = _time(lambda: ctx.costmap(polys, t.nx, t.ny, t.cell, t.x0, t.y0), steps, 3, stream, flush)
     out["costmap"] = {"workload": f"2048^2 nodes, {len(polys)} perimeters, {nv} edges", "ms": ms,
                       "node_edge_pairs_per_s": 2048 * 2048 * nv / (ms / 1e3)}
+    # the adjoint's configuration: 64 candidates of the plain plan at H = 100, dt = 0.02 s
+    wa = gen.workload_plain(0, N=64, H=100, dt=0.02)
+    tera = ctx.terrain_prepare(torch.as_tensor(wa.terrain.heights).to(dev), wa.terrain.cell)
+    ca = torch.as_tensor(wa.ctrl).to(dev)
+    xa = [float(v) for v in wa.x0]
+    ms = _time(lambda: ctx.grad(wa.vehicle, wa.cost, tera, xa, ca, wa.dt, wa.n_sub, 10), steps, 3, stream, flush)
+    out["adjoint"] = {"workload": "dJ/dctrl of 64 candidates, H = 100, dt = 0.02 s (4 Euler steps), "
+                                  "checkpoints every 10 steps", "ms": ms,
+                      "candidate_gradients_per_s": 64 / (ms / 1e3)}
+    # the sampler: the largest serving request, 32768 candidates x 150 steps
+    ctrl_s = torch.empty((150, 32768, 2), dtype=torch.float32, device=dev)
+    ms = _time(lambda: ctx.sample(32768, 150, 0.2, 0.3, (1, 2), 3, out=ctrl_s), steps, 3, stream, flush)
+    out["sampler"] = {"workload": "32768 candidates x 150 steps, Philox4x64-10 + Box-Muller", "ms": ms,
+                      "hbm_gbs": 150 * 32768 * 8 / (ms / 1e3) / 1e9}
     return out
 
 

@@ -156,6 +156,34 @@ class _Batch:
     t_launch: float
 
 
+def admit(queue, vehicles, max_batch: int, slot_candidates: int, alloc):
+    """One admission pass over the arrived requests, in arrival order: a
+    request joins the batch if its vehicle has no plan in flight and no
+    earlier request still waiting, the batch has room (max_batch requests,
+    slot_candidates candidates) and alloc(request) finds it device memory
+    (an offset, or None).  Returns (batch, offsets, requests kept waiting);
+    admitted vehicles are marked busy."""
+    batch, blocks, keep, cands = [], [], [], 0
+    waiting = set()                       # vehicles with an earlier request kept back
+    for r in queue:
+        v = vehicles[r.vehicle]
+        if (v.busy or r.vehicle in waiting or len(batch) >= max_batch or
+                cands + r.N > slot_candidates):
+            keep.append(r)
+            waiting.add(r.vehicle)
+            continue
+        off = alloc(r)
+        if off is None:                   # no memory: wait for completions
+            keep.append(r)
+            waiting.add(r.vehicle)
+            continue
+        v.busy = True
+        batch.append(r)
+        blocks.append(off)
+        cands += r.N
+    return batch, blocks, keep
+
+
 class Server:
     """Continuous batching over `streams` CUDA streams (one atp context each)."""
 
@@ -237,22 +265,8 @@ class Server:
             for s in range(len(self.streams)):
                 if self.inflight[s] is not None or not queue:
                     continue
-                batch, blocks, cands, keep = [], [], 0, []
-                for r in queue:
-                    v = self.vehicles[r.vehicle]
-                    if (v.busy or len(batch) >= self.max_batch or
-                            cands + r.N > self.slot_candidates):
-                        keep.append(r)
-                        continue
-                    off = self.arena.alloc(request_layout(r.N, r.H)[1])
-                    if off is None:               # no memory: wait for completions
-                        keep.append(r)
-                        continue
-                    v.busy = True
-                    batch.append(r)
-                    blocks.append(off)
-                    cands += r.N
-                queue = keep
+                batch, blocks, queue = admit(queue, self.vehicles, self.max_batch, self.slot_candidates,
+                                             lambda r: self.arena.alloc(request_layout(r.N, r.H)[1]))
                 if not batch:
                     continue
                 stream = self.streams[s]
@@ -343,8 +357,12 @@ def resident_vehicles(fleet, device: int = 0, h_max: int = 150):
 
 
 def reset_warm_start(vehicles):
-    """Forget every vehicle's previous plan (before replaying a trace)."""
+    """Forget every vehicle's previous plan (before replaying a trace).  The
+    clears run on the current stream and the server's streams do not wait for
+    it, so this waits for the device before returning."""
+    import torch
     for v in vehicles:
         v.prev.zero_()
         v.prev_H = 0
         v.busy = False
+    torch.cuda.synchronize()

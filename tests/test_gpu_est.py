@@ -136,3 +136,27 @@ def test_est_invalid_arguments(ctx):
         ctx.plan_est(w.vehicle, w.cost, ter, [float("nan")] * 7, dev(w.ctrl), w.dt)
     with pytest.raises(atp.AtpError, match="INVALID"):
         ctx.plan_est(w.vehicle, w.cost, ter, [float(v) for v in w.x0], dev(w.ctrl), 0.0)
+
+
+def test_est_bf16_terrain_against_decoded_oracle(ctx):
+    """The planar model on BF16 texels against the oracle fed the same decoded
+    terrain (the host restatement of the format), which leaves arithmetic
+    error only."""
+    from paper_2603_20525_gb300 import atp
+    w = gen.workload_est(3)
+    t = w.terrain
+    ter = ctx.terrain_prepare(dev(t.heights), t.cell, t.x0, t.y0, fmt=atp.BF16X4)
+    o = ctx.plan_est(w.vehicle, w.cost, ter, [float(v) for v in w.x0], dev(w.ctrl), w.dt, w.n_sub,
+                     want_xf=True)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in o.items() if k != "out"}
+    g.update(atp.decode_out(o["out"]))
+    g["xf"] = g["xf"].T.copy()
+    h_dec, gx, gy, _, _ = oracle.bf16_terrain(t.heights, t.cell)
+    od = oracle.Terrain(h_dec, t.cell, t.x0, t.y0, gx=gx, gy=gy)
+    ref = oracle.est_plan(w.vehicle, w.cost, od, w.x0, w.ctrl, w.dt, w.n_sub)
+    sens = parity.conditioning(oracle, w.vehicle, w.cost, od, w.x0, w.ctrl, w.dt, w.n_sub, ref, model="est")
+    v = parity.classify(g, ref, sens, w.vehicle, model="est")
+    print("est bf16 vs decoded oracle", v["stats"])
+    assert v["stats"]["fails"] == 0 and v["stats"]["tail"] <= v["stats"]["cap"]
+    assert g["best_idx"] == lexmin(g["cost"], g["flags"])

@@ -29,10 +29,14 @@ def burst_trace():
     return [serve.Request(i, v, N, H, dt, t) for i, (t, v, N, H, dt) in enumerate(reqs)]
 
 
-def test_served_equals_sequential_bitwise(fleet):
+@pytest.mark.parametrize("slots", [1 << 16, 20000])
+def test_served_equals_sequential_bitwise(fleet, slots):
+    """With ample slots, and with slots so tight that the admission keeps
+    requests back (each vehicle's later requests must then wait behind them,
+    or the warm starts would differ)."""
     from paper_2603_20525_gb300 import serve
     vehicles = serve.resident_vehicles(fleet)
-    srv = serve.Server(vehicles, streams=2, slot_candidates=1 << 16, arena_bytes=256 << 20)
+    srv = serve.Server(vehicles, streams=2, slot_candidates=slots, arena_bytes=256 << 20)
     trace = burst_trace()
     served = srv.serve(trace)
     serve.reset_warm_start(vehicles)

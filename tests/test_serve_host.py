@@ -70,3 +70,65 @@ def test_request_layout_is_aligned_and_disjoint():
     offs = [o for _, o, _, _ in lay]
     assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
     assert total >= 16384 * 100 * 8 + 16384 * 9 + 100 * 12 + 24
+
+
+def test_admission_keeps_each_vehicles_order():
+    """A request that does not fit (slots, batch size or memory) holds back
+    every later request of its vehicle, so a vehicle's plans, and its warm
+    starts, always run in arrival order; other vehicles fill the batch."""
+    from paper_2603_20525_gb300 import serve
+
+    class V:
+        busy = False
+
+    vehicles = [V(), V(), V()]
+    q = [serve.Request(0, 0, 4096, 50, 0.02, 0.0),       # fits
+         serve.Request(1, 1, 65536, 50, 0.02, 0.0),      # too many candidates now
+         serve.Request(2, 1, 1024, 50, 0.02, 0.0),       # same vehicle: must wait behind rid 1
+         serve.Request(3, 2, 1024, 50, 0.02, 0.0),       # other vehicle: fits
+         serve.Request(4, 0, 1024, 50, 0.02, 0.0)]       # vehicle 0 is now busy
+    batch, offs, keep = serve.admit(q, vehicles, 64, 65536, lambda r: 0)
+    assert [r.rid for r in batch] == [0, 3] and [r.rid for r in keep] == [1, 2, 4]
+    assert vehicles[0].busy and vehicles[2].busy and not vehicles[1].busy
+    # memory refusal holds back the vehicle too
+    for v in vehicles:
+        v.busy = False
+    mem = iter([None, 0, 0])
+    batch, offs, keep = serve.admit(q[1:4], vehicles, 64, 1 << 20, lambda r: next(mem))
+    assert [r.rid for r in batch] == [3] and [r.rid for r in keep] == [1, 2]
+    # the batch limit holds back later requests of a vehicle as well
+    for v in vehicles:
+        v.busy = False
+    batch, offs, keep = serve.admit([q[0], q[3], q[4]], vehicles, 1, 1 << 20, lambda r: 0)
+    assert [r.rid for r in batch] == [0] and [r.rid for r in keep] == [3, 4]
+
+
+def test_admission_replays_arrival_order_under_backlog():
+    """Against a random backlog with tight slots and memory, every vehicle's
+    admitted requests come out in arrival order."""
+    import numpy as np
+    from paper_2603_20525_gb300 import serve
+
+    class V:
+        busy = False
+
+    rng = np.random.default_rng(0)
+    vehicles = [V() for _ in range(8)]
+    queue = [serve.Request(i, int(rng.integers(0, 8)), int(rng.choice([1024, 4096, 16384, 32768])), 50, 0.02, 0.0)
+             for i in range(400)]
+    order = {v: [] for v in range(8)}
+    free = [5]
+    while queue:
+        def alloc(r):
+            if free[0] > 0 and rng.random() < 0.8:
+                free[0] -= 1
+                return 0
+            return None
+        batch, offs, queue = serve.admit(queue, vehicles, 6, 40000, alloc)
+        for r in batch:
+            order[r.vehicle].append(r.rid)
+            vehicles[r.vehicle].busy = False          # completes before the next pass
+        free[0] = 5
+    for v, rids in order.items():
+        assert rids == sorted(rids)
+    assert sum(len(r) for r in order.values()) == 400
