@@ -76,6 +76,24 @@ def recorded_traffic(workload):
     return int(kv["dram_bytes_per_launch"])
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks: the job's time is its slowest rank's.
+    One rank (or no process group) returns x."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world_size: int, units_per_rank: float, ms: float) -> float:
+    """Weak scaling: every rank runs units_per_rank; the job's rate is all
+    ranks' units over the slowest rank's time (ms)."""
+    return world_size * units_per_rank / (ms / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -403,12 +421,9 @@ def main():
     per_step = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(per_step)
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     units = w.N * w.H
-    value = ws * units / (ms / 1000)
+    value = job_rate(ws, units, ms)
 
     # end to end through the public API with host buffers
     ctrl_h = torch.as_tensor(w.ctrl).pin_memory()
@@ -437,10 +452,7 @@ def main():
         ee[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in ee)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
     h2d = ctrl_h.numel() * 4 + (x0_h.numel() * 4 if per else 0)
     d2h = sum(v.numel() * v.element_size() for v in res_h.values())
 
@@ -463,7 +475,7 @@ def main():
                          "note": f"{FLOPS_PER_SUBSTEP} algorithmic FP32 flops per Euler step x "
                                  f"{substeps} Euler steps per launch; peak = 152 SMs x 128 FP32 "
                                  f"lanes x 2 x 2070 MHz (derived)"},
-            "e2e": {"value": ws * units / (e2e_ms / 1000), "unit": "rollout-steps/s",
+            "e2e": {"value": job_rate(ws, units, e2e_ms), "unit": "rollout-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": args.steps,
             "clocks": clk,
