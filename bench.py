@@ -280,6 +280,7 @@ def run_variants(ctx, dev, stream, flush, steps=10):
     costmap) on a 2048^2 map at 0.1 m."""
     import gen
     import torch
+    from paper_2603_20525_gb300 import atp
     out = {}
     w = gen.workload_est(0, N=16384, H=100, dt=0.02, scaled=True)
     ter = ctx.terrain_prepare(torch.as_tensor(w.terrain.heights).to(dev), w.terrain.cell,
@@ -293,6 +294,17 @@ def run_variants(ctx, dev, stream, flush, steps=10):
                                    f"({w.n_sub} Euler steps), 1024^2 map, 1.5 m level of detail",
                        "ms_per_plan": ms, "rollout_steps_per_s": w.N * w.H / (ms / 1e3),
                        "substeps_per_s": w.N * w.H * w.n_sub / (ms / 1e3)}
+    # the scaled plan on BF16 texels (8 B per node instead of 16)
+    ws = gen.workload_scaled(0)
+    ter16 = ctx.terrain_prepare(torch.as_tensor(ws.terrain.heights).to(dev), ws.terrain.cell,
+                                ws.terrain.x0, ws.terrain.y0, fmt=atp.BF16X4)
+    ctrl16 = torch.as_tensor(ws.ctrl).to(dev)
+    x016 = torch.as_tensor(np.ascontiguousarray(ws.x0.T)).to(dev)
+    o16 = ctx.plan(ws.vehicle, ws.cost, ter16, x016, ctrl16, ws.dt, ws.n_sub, want_candidates=False)
+    ms = _time(lambda: ctx.plan(ws.vehicle, ws.cost, ter16, x016, ctrl16, ws.dt, ws.n_sub, out=o16),
+               steps, 3, stream, flush)
+    out["bf16_terrain_plan"] = {"workload": "the scaled plan on BF16 texels", "ms_per_plan": ms,
+                                "rollout_steps_per_s": ws.N * ws.H / (ms / 1e3)}
     t = gen.terrain_tile(2048, 5, lod_sigma=0.0)
     h = torch.as_tensor(t.heights).to(dev)
     sm = torch.empty_like(h)

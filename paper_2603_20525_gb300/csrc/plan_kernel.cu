@@ -258,8 +258,11 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
 
 }
 
+// Register budgets, from A/B runs on the GB300: four lanes run best with
+// ptxas free to use about 104 registers (minimum 1 CTA per SM), one and two
+// lanes with the 128-register cap of 8 resident 64-thread CTAs per SM.
 template <int LANES, bool PER_X0, bool REDUCE, int TEX>
-__global__ void __launch_bounds__(kPlanBlock)
+__global__ void __launch_bounds__(kPlanBlock, LANES == 4 ? 1 : 8)
 plan_kernel(const __grid_constant__ PlanParams p)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
