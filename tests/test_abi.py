@@ -48,8 +48,10 @@ def test_struct_layout_matches_header():
 #define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
   P(atp_vehicle) P(atp_cost) P(atp_state) P(atp_terrain) P(atp_plan_out)
+  P(atp_est_state) P(atp_plan_request)
   O(atp_vehicle, g) O(atp_cost, goal_r) O(atp_state, delta) O(atp_terrain, format)
-  O(atp_terrain, cell) O(atp_plan_out, best_min_step)
+  O(atp_terrain, cell) O(atp_terrain, flags) O(atp_plan_out, best_min_step)
+  O(atp_est_state, vx) O(atp_plan_request, cand_xf_dev) O(atp_plan_request, dt)
   return 0;
 }
 '''
@@ -71,6 +73,12 @@ int main(void) {
     assert int(out["atp_terrain.format"]) == atp.TerrainC.format.offset
     assert int(out["atp_terrain.cell"]) == atp.TerrainC.cell.offset
     assert int(out["atp_plan_out.best_min_step"]) == atp.PlanOut.best_min_step.offset
+    assert int(out["atp_terrain.flags"]) == atp.TerrainC.flags.offset
+    assert int(out["atp_est_state"]) == C.sizeof(atp.EstState)
+    assert int(out["atp_est_state.vx"]) == atp.EstState.vx.offset
+    assert int(out["atp_plan_request"]) == C.sizeof(atp.PlanRequest)
+    assert int(out["atp_plan_request.cand_xf_dev"]) == atp.PlanRequest.cand_xf_dev.offset
+    assert int(out["atp_plan_request.dt"]) == atp.PlanRequest.dt.offset
 
 
 def test_no_cpu_fallback_path():
