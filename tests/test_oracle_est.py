@@ -243,3 +243,77 @@ def test_goal_truncation_and_feasibility_flags():
     c2 = dict(w.cost, goal_x=float(x0[0]), goal_y=float(x0[1]))
     r2 = oracle.est_rollout(w.vehicle, c2, t, x0, w.ctrl[:, :4], w.dt, w.n_sub)
     assert np.all(r2["J"] == 0.0) and np.all(r2["flags"] & oracle.DONE)
+
+
+# The longitudinal acceleration of the CoM in B includes the transport term
+# a_Bx = v_x' - w_z v_y, which moves load between the axles in a turn.
+def test_axle_load_transfer_uses_body_acceleration():
+    v = VEH
+    L = v["Lf"] + v["Lr"]
+    vy, wz, acc = 0.7, 0.4, 1.5
+    _, d = oracle.est_evaluate(v, no_goal(), plane(), est_state(vy=vy, wz=wz), [0.0, acc])
+    a = acc - wz * vy
+    assert d["aBx"] == pytest.approx(a, rel=1e-12)
+    assert d["Fzf"] == pytest.approx(v["M"] * v["g"] * v["Lr"] / L - v["M"] * v["hR"] * a / L, rel=1e-12)
+
+
+# On a side slope with no slip yet the tires carry no lateral force: the body
+# accelerates downhill at g sin(beta), and the lateral-acceleration margin,
+# which measures only what the tires transmit (a_By - g_By), is the full abar.
+def test_side_slope_without_slip_slides_and_keeps_full_margin():
+    v = VEH
+    beta = math.atan(0.25)
+    t = plane(0.0, 0.25)
+    xd, d = oracle.est_evaluate(v, no_goal(), t, est_state(vx=6.0), [0.0, 0.0])
+    assert d["Fyf"] == 0.0 and d["Fyr"] == 0.0
+    assert xd[3] == pytest.approx(-v["g"] * math.sin(beta), rel=1e-12)
+    assert d["margin"] == pytest.approx(v["g"] * v["e"] / (2 * v["hR"]), rel=1e-12)
+
+
+# Planar velocity: on level ground v_W is v_B turned by the yaw, whatever the
+# side slip.
+def test_world_velocity_is_body_velocity_turned_by_yaw():
+    psi, vx, vy = 0.9, 7.0, -1.3
+    xd, _ = oracle.est_evaluate(VEH, no_goal(), plane(), est_state(psi=psi, vx=vx, vy=vy), [0.0, 0.0])
+    Rz = Rotation.from_euler("z", psi).as_matrix()
+    np.testing.assert_allclose(xd[:2], (Rz @ [vx, vy, 0.0])[:2], rtol=0, atol=1e-12)
+
+
+# Yaw moment of the steered front tire: its force acts along the wheel's own
+# lateral axis, turned by delta; the moment about the CoM is the cross
+# product of the axle position with that force (numpy.cross, scipy rotation).
+@pytest.mark.parametrize("delta", [0.3, -0.55])
+def test_steered_front_force_yaw_moment(delta):
+    v = VEH
+    vx = 6.0
+    _, d = oracle.est_evaluate(v, no_goal(), plane(), est_state(delta=delta, vx=vx), [0.0, 0.0])
+    xd, _ = oracle.est_evaluate(v, no_goal(), plane(), est_state(delta=delta, vx=vx), [0.0, 0.0])
+    f_wheel = Rotation.from_euler("z", delta).apply([0.0, d["Fyf"], 0.0])
+    Mz = np.cross([v["Lf"], 0.0, 0.0], f_wheel)[2] + np.cross([-v["Lr"], 0.0, 0.0], [0.0, d["Fyr"], 0.0])[2]
+    assert xd[4] == pytest.approx(Mz / v["Jzz"], rel=1e-12)
+
+
+# Goal circle inclusive, steering rate and angle clamps, and the feasibility
+# threshold, by hand on level ground.
+def test_goal_inclusive_and_clamps_and_feasibility():
+    v = VEH
+    t = plane(n=400, cell=0.5, x0=-100.0, y0=-100.0)
+    # goal exactly 1 m ahead, reached after 64 dyadic Euler steps of 1/64 m
+    c = dict(gen.cost_default(1.0, 0.0), goal_r=0.0)
+    ctrl = np.zeros((4, 1, 2), np.float32)
+    r = oracle.est_rollout(v, c, t, est_state(vx=4.0).astype(np.float32), ctrl, 0.125, 32)
+    assert r["flags"][0] & oracle.DONE and r["xf"][0][0] == pytest.approx(1.0, abs=1e-12)
+    # a steering rate beyond the limit is clamped; the angle stops at delta_max
+    ctrl = np.zeros((20, 1, 2), np.float32)
+    ctrl[:, 0, 0] = 5.0
+    st = oracle.est_trajectory(v, no_goal(), t, est_state(vx=1.0), ctrl[:, 0, :], 0.1, 20)
+    assert st[20, 5] == pytest.approx(0.1 * v["delta_rate_max"], rel=1e-9)
+    assert st[-1, 5] == pytest.approx(v["delta_max"], rel=1e-15)
+    # feasibility: margin > 0 strictly
+    vh = dict(v, mu=2.5)
+    ctrl = np.zeros((40, 2, 2), np.float32)
+    ctrl[:, 0, 0] = 0.25                    # stays inside the bound
+    ctrl[:, 1, 0] = 0.3                     # just crosses it (margin between -1 and 0)
+    r = oracle.est_rollout(vh, no_goal(), t, est_state(vx=8.0).astype(np.float32), ctrl, 0.05, 10)
+    assert r["margin"][0] > 0 and r["flags"][0] & oracle.FEASIBLE
+    assert -1.0 < r["margin"][1] < 0 and not r["flags"][1] & oracle.FEASIBLE

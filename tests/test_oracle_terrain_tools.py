@@ -126,3 +126,38 @@ def test_costmap_soft_constraint_values_and_sum():
     both = [(SQUARE, 0), (SQUARE, 0)]
     c3, _ = oracle.costmap(both, 21, 1, 0.25, -1.0, 1.0, eps, sig)
     np.testing.assert_allclose(c3, 2 * c, rtol=1e-15)
+
+
+def _winding(poly, x, y):
+    """Winding number of a closed polygon around (x, y) (Sunday's crossing
+    test with orientation signs): an inside test independent of the oracle's
+    even-odd ray rule."""
+    wn = 0
+    n = len(poly)
+    for k in range(n):
+        (ax, ay), (bx, by) = poly[k], poly[(k + 1) % n]
+        cross = (bx - ax) * (y - ay) - (x - ax) * (by - ay)
+        if ay <= y < by and cross > 0:
+            wn += 1
+        elif by <= y < ay and cross < 0:
+            wn -= 1
+    return wn
+
+
+# Points exactly at the height of vertices (where a ray passes through a
+# vertex), for a diamond, a star with notches and a polygon with a horizontal
+# edge, against the winding number.
+def test_inside_rule_at_vertex_heights():
+    star = [(math.cos(a) * (2.0 if k % 2 == 0 else 0.8), math.sin(a) * (2.0 if k % 2 == 0 else 0.8))
+            for k, a in enumerate(np.linspace(0, 2 * np.pi, 10, endpoint=False))]
+    shapes = [[(0, 1), (1, 0), (0, -1), (-1, 0)], star, [(0, 0), (3, 0), (3, 1), (2, 1), (2, 2), (0, 2)]]
+    rng = np.random.default_rng(5)
+    for poly in shapes:
+        ys = sorted({float(p[1]) for p in poly})
+        for _ in range(300):
+            y = ys[rng.integers(len(ys))]
+            x = rng.uniform(-3, 4)
+            s = oracle.sdist(poly, 0, x, y)
+            if abs(s) < 1e-9:
+                continue                      # on the perimeter
+            assert (s < 0) == (_winding(poly, x, y) != 0), (poly, x, y, s)
