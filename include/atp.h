@@ -269,8 +269,8 @@ int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *
  *             zero for a steering rate beyond its limit (the clamp)
  *   ckpt      control steps between stored states (0 selects 10); the
  *             reverse pass recomputes one such segment at a time, so memory
- *             is (H / ckpt + ckpt n_sub) x 80 bytes per candidate.
- * One thread per candidate; F32X4 terrain only. */
+ *             is (H / ckpt + ckpt n_sub) x 320 bytes per candidate.
+ * Four threads per candidate (one wheel each); F32X4 terrain only. */
 int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
              const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int K, int H, float dt,
              int n_sub, int ckpt, float *cost_dev, float *grad_dev, void *stream);

@@ -2,9 +2,13 @@
 // (arxiv 2603.20525, Sec. IV-A..IV-C): dJ/du for the raw control sequence u
 // of each of K candidates, J = sum over Euler steps of h L + Phi.
 //
-// One thread per candidate.  The forward pass stores the state every
-// `ckpt` control steps; the reverse pass recomputes one segment at a time
-// into a per-thread buffer and walks its Euler steps backwards.  Each
+// Four threads per candidate, one wheel each, as in the plan kernel's
+// four-lane layout: every lane repeats the body arithmetic and its adjoint
+// bit-identically, runs its own wheel forwards and backwards, and the quad
+// exchanges only sums (the force and moment sums forwards; the wheels'
+// contributions to the body adjoints backwards).  The forward pass stores the
+// state every `ckpt` control steps; the reverse pass recomputes one segment
+// at a time into a per-lane buffer and walks its Euler steps backwards.  Each
 // backward step recomputes the step's intermediates from the stored state
 // and propagates the state adjoint lambda through the Euler update, the state
 // derivative A(xi) + B zeta, the force and moment sums, every wheel (contact
@@ -45,6 +49,36 @@ __device__ __forceinline__ void st_load(const float *src, size_t stride, St &s)
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// sum over the four lanes of a candidate (the same bits in every lane)
+__device__ __forceinline__ float qsum(float v, unsigned mask)
+{
+    v += __shfl_xor_sync(mask, v, 1);
+    v += __shfl_xor_sync(mask, v, 2);
+    return v;
+}
+
+// this lane's wheel: fl, fr, rl, rr for q = 0..3
+struct Lane {
+    int q;
+    unsigned mask;
+    bool front;
+    float rx, ry, k, b, Fs;
+};
+
+__device__ __forceinline__ Lane lane_of(const Veh &V, int q, unsigned mask)
+{
+    Lane l;
+    l.q = q;
+    l.mask = mask;
+    l.front = q < 2;
+    l.rx = l.front ? V.Lf : -V.Lr;
+    l.ry = (q & 1) ? -V.he : V.he;
+    l.k = l.front ? V.kf : V.kr;
+    l.b = l.front ? V.bf : V.br;
+    l.Fs = l.front ? V.Fsf : V.Fsr;
+    return l;
+}
 
 // a lookup axis: cell, weight and whether the query was clamped
 __device__ __forceinline__ int axis_c(int ic, float fc, float o, float inv_cell, int n, float &a, bool &clamped)
@@ -230,9 +264,9 @@ struct StepOut {
     bool stepped;     // false: the goal was reached before this step
 };
 
-// One forward Euler step (the single-lane arithmetic of the plan kernel);
+// One forward Euler step (the four-lane arithmetic of the plan kernel);
 // returns the running cost rate.
-__device__ __forceinline__ StepOut step_fwd(const GradParams &p, St &s, float dd, float ax)
+__device__ __forceinline__ StepOut step_fwd(const GradParams &p, St &s, float dd, float ax, const Lane &ln)
 {
     const Veh &V = p.V;
     const Cost &Cc = p.C;
@@ -265,20 +299,16 @@ __device__ __forceinline__ StepOut step_fwd(const GradParams &p, St &s, float dd
     cell_split(s.x, s.xl, T.inv_cell, icx, fcx);
     cell_split(s.y, s.yl, T.inv_cell, icy, fcy);
     const float gBx = -V.g * R[6], gBy = -V.g * R[7], gBz = -V.g * R[8];
-    WF w[4];
-    const float rxs[4] = {V.Lf, V.Lf, -V.Lr, -V.Lr}, rys[4] = {V.he, -V.he, V.he, -V.he};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        wheel_fwd(V, T, R, icx, fcx, icy, fcy, s.z, s.zl, s.vx, s.vy, s.vz, s.wx, s.wy, s.wz, rxs[i], rys[i],
-                  i < 2 ? V.kf : V.kr, i < 2 ? V.bf : V.br, i < 2 ? V.Fsf : V.Fsr, i < 2 ? s.d : 0.f, w[i]);
-    const float Fyf = (w[0].Fy + w[1].Fy) * cd;
-    const float Fyr = w[2].Fy + w[3].Fy;
-    const float FyB = Fyf + Fyr;
-    const float FzB = (w[0].Fz + w[1].Fz) + (w[2].Fz + w[3].Fz);
-    const float Mx = fmaf(V.hR, FyB, V.he * ((w[0].Fz - w[1].Fz) + (w[2].Fz - w[3].Fz)));
-    float My = fmaf(V.Lr, w[2].Fz + w[3].Fz, -V.Lf * (w[0].Fz + w[1].Fz));
-    const float Mz = fmaf(V.Lf, Fyf, -V.Lr * Fyr);
-    const float csum = (w[0].t.w + w[1].t.w) + (w[2].t.w + w[3].t.w);
+    WF w;
+    wheel_fwd(V, T, R, icx, fcx, icy, fcy, s.z, s.zl, s.vx, s.vy, s.vz, s.wx, s.wy, s.wz, ln.rx, ln.ry, ln.k,
+              ln.b, ln.Fs, ln.front ? s.d : 0.f, w);
+    const float fy = ln.front ? w.Fy * cd : w.Fy;
+    const float FyB = qsum(fy, ln.mask);
+    const float FzB = qsum(w.Fz, ln.mask);
+    const float Mx = fmaf(V.hR, FyB, qsum(ln.ry * w.Fz, ln.mask));
+    float My = qsum(-ln.rx * w.Fz, ln.mask);
+    const float Mz = qsum(ln.rx * fy, ln.mask);
+    const float csum = T.has_cm ? qsum(w.t.w, ln.mask) : 0.f;
     const float Fx = V.halfM * fmaf(-s.wz, s.vy, fmaf(s.wy, s.vz, ax - gBx));
     My = fmaf(-V.hR, 2.f * Fx, My);
     const float soft = fmaxf(fmaf(-U, Cc.inv_eps, 1.f), 0.f);
@@ -318,7 +348,7 @@ __device__ __forceinline__ StepOut step_fwd(const GradParams &p, St &s, float dd
 // after the step on entry and of the state before it on exit; g_dd and g_ax
 // receive the step's contributions to dJ/d(steering rate) and dJ/d(accel).
 __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, float lam[13], float &g_dd,
-                         float &g_ax)
+                         float &g_ax, const Lane &ln)
 {
     const Veh &V = p.V;
     const Cost &Cc = p.C;
@@ -345,12 +375,9 @@ __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, f
     cell_split(s.x, s.xl, T.inv_cell, icx, fcx);
     cell_split(s.y, s.yl, T.inv_cell, icy, fcy);
     const float vx = s.vx, vy = s.vy, vz = s.vz, wx = s.wx, wy = s.wy, wz = s.wz;
-    WF w[4];
-    const float rxs[4] = {V.Lf, V.Lf, -V.Lr, -V.Lr}, rys[4] = {V.he, -V.he, V.he, -V.he};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        wheel_fwd(V, T, R, icx, fcx, icy, fcy, s.z, s.zl, vx, vy, vz, wx, wy, wz, rxs[i], rys[i],
-                  i < 2 ? V.kf : V.kr, i < 2 ? V.bf : V.br, i < 2 ? V.Fsf : V.Fsr, i < 2 ? s.d : 0.f, w[i]);
+    WF w;
+    wheel_fwd(V, T, R, icx, fcx, icy, fcy, s.z, s.zl, vx, vy, vz, wx, wy, wz, ln.rx, ln.ry, ln.k, ln.b, ln.Fs,
+              ln.front ? s.d : 0.f, w);
     const float soft = fmaxf(fmaf(-U, Cc.inv_eps, 1.f), 0.f);
     const float ic = rcp(cth);
     const float wsc = fmaf(sph, wy, cph * wz);
@@ -434,27 +461,35 @@ __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, f
     ad.vz += a_Fx * V.halfM * wy;
     ad.wz -= a_Fx * V.halfM * vy;
     ad.vy -= a_Fx * V.halfM * wz;
-    // sums
+    // sums: FyB = sum fy, Mx = hR FyB + sum ry Fz, My = sum -rx Fz (+ the
+    // constraint force), Mz = sum rx fy, with fy = Fy cos(delta) in front
     const float a_FyB = a_FyB0 + V.hR * a_Mx;
-    const float a_Fyf = a_FyB + V.Lf * a_Mz;
-    const float a_Fyr = a_FyB - V.Lr * a_Mz;
-    const float a_cd = a_Fyf * (w[0].Fy + w[1].Fy);
-    a_d -= sd * a_cd;
-    float aFy[4] = {a_Fyf * cd, a_Fyf * cd, a_Fyr, a_Fyr};
-    float aFz[4];
-    aFz[0] = a_FzB + V.he * a_Mx - V.Lf * a_My;
-    aFz[1] = a_FzB - V.he * a_Mx - V.Lf * a_My;
-    aFz[2] = a_FzB + V.he * a_Mx + V.Lr * a_My;
-    aFz[3] = a_FzB - V.he * a_Mx + V.Lr * a_My;
+    const float a_fy = a_FyB + ln.rx * a_Mz;
+    const float aFy = ln.front ? a_fy * cd : a_fy;
+    const float aFz = a_FzB + ln.ry * a_Mx - ln.rx * a_My;
     // gravity in B
     ad.R[6] -= V.g * a_gBx;
     ad.R[7] -= V.g * a_gBy;
     ad.R[8] -= V.g * a_gBz;
-    // wheels
+    // this lane's wheel into its own accumulator, then the quad's sum
+    Adj aw;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        wheel_adj(V, T, R, wx, wy, rxs[i], rys[i], i < 2 ? V.kf : V.kr, i < 2 ? V.bf : V.br, i < 2 ? 1.f : 0.f,
-                  w[i], aFz[i], aFy[i], a_csum, ad, a_d);
+    for (int c = 0; c < 9; ++c) aw.R[c] = 0.f;
+    aw.x = aw.y = aw.z = aw.vx = aw.vy = aw.vz = aw.wx = aw.wy = aw.wz = aw.d = 0.f;
+    float a_dw = ln.front ? -sd * a_fy * w.Fy : 0.f;                // cos(delta) of the front forces
+    wheel_adj(V, T, R, wx, wy, ln.rx, ln.ry, ln.k, ln.b, ln.front ? 1.f : 0.f, w, aFz, aFy, a_csum, aw, a_dw);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ad.R[c] += qsum(aw.R[c], ln.mask);
+    ad.x += qsum(aw.x, ln.mask);
+    ad.y += qsum(aw.y, ln.mask);
+    ad.z += qsum(aw.z, ln.mask);
+    ad.vx += qsum(aw.vx, ln.mask);
+    ad.vy += qsum(aw.vy, ln.mask);
+    ad.vz += qsum(aw.vz, ln.mask);
+    ad.wx += qsum(aw.wx, ln.mask);
+    ad.wy += qsum(aw.wy, ln.mask);
+    ad.wz += qsum(aw.wz, ln.mask);
+    a_d += qsum(a_dw, ln.mask);
     // ESM: U = +/- M g Rbar (1 - (sin|phi| cos phibar + cos phi sin phibar)) cos theta
     {
         const float sg = fabsf(s.ph) < V.tip ? 1.f : -1.f;
@@ -493,13 +528,16 @@ __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, f
     lam[12] = a_d;
 }
 
-__global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradParams p)
+__global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ GradParams p)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= p.K) return;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = tid / kGradLanes;
+    if (j >= p.K) return;                       // whole quads leave together
+    const Lane ln = lane_of(p.V, tid & (kGradLanes - 1), 0xfu << (threadIdx.x & 28));
     const Terrain &T = p.T;
     const Cost &Cc = p.C;
     const size_t K = (size_t)p.K;
+    const size_t KL = K * kGradLanes;           // every lane keeps its own copy of the states
     St s;
     {
         float q[13];
@@ -520,18 +558,18 @@ __global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradPa
         s.zl = s.psil = s.vxl = s.vyl = s.vzl = 0.f;
     }
     const int n_seg = (p.H + p.ckpt - 1) / p.ckpt;
-    float *ck = p.ckpt_buf + j;                   // [n_seg][20][K]
-    float *seg = p.seg_buf + j;                   // [ckpt * n_sub][20][K]
+    float *ck = p.ckpt_buf + tid;                 // [n_seg][20][K lanes]
+    float *seg = p.seg_buf + tid;                 // [ckpt * n_sub][20][K lanes]
     // forward: cost and checkpoints
     float J = 0.f;
     bool done = false;
     int done_step = p.H * p.n_sub;               // Euler step index where the goal stopped the rollout
     for (int k = 0; k < p.H; ++k) {
-        if (k % p.ckpt == 0) st_store(ck + (size_t)(k / p.ckpt) * kStFloats * K, K, s);
+        if (k % p.ckpt == 0) st_store(ck + (size_t)(k / p.ckpt) * kStFloats * KL, KL, s);
         const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
         const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
         for (int q = 0; q < p.n_sub && !done; ++q) {
-            const StepOut o = step_fwd(p, s, dd, u.y);
+            const StepOut o = step_fwd(p, s, dd, u.y, ln);
             if (!o.stepped) {
                 done = true;
                 done_step = k * p.n_sub + q;
@@ -545,7 +583,7 @@ __global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradPa
     const float gdy = (s.y - Cc.gy_hi) + (s.yl - Cc.gy_lo);
     const float dist = sqrtf(fmaf(gdx, gdx, gdy * gdy));
     J = fmaf(Cc.wg, dist, J);
-    p.cost[j] = J;
+    if (ln.q == 0) p.cost[j] = J;
     float lam[13];
 #pragma unroll
     for (int c = 0; c < 13; ++c) lam[c] = 0.f;
@@ -557,7 +595,7 @@ __global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradPa
     for (int sg = n_seg - 1; sg >= 0; --sg) {
         const int k0 = sg * p.ckpt, k1 = min(p.H, k0 + p.ckpt);
         St r;
-        st_load(ck + (size_t)sg * kStFloats * K, K, r);
+        st_load(ck + (size_t)sg * kStFloats * KL, KL, r);
         // recompute the segment's Euler-step start states
         int n_steps = 0;
         for (int k = k0; k < k1; ++k) {
@@ -566,9 +604,9 @@ __global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradPa
             for (int q = 0; q < p.n_sub; ++q) {
                 const int e = k * p.n_sub + q;
                 if (e >= done_step) break;
-                st_store(seg + (size_t)n_steps * kStFloats * K, K, r);
+                st_store(seg + (size_t)n_steps * kStFloats * KL, KL, r);
                 ++n_steps;
-                step_fwd(p, r, dd, u.y);
+                step_fwd(p, r, dd, u.y, ln);
             }
         }
         // walk the segment's steps backwards
@@ -582,12 +620,14 @@ __global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradPa
                 if (e >= done_step) continue;
                 const int local = e - k0 * p.n_sub;
                 St r2;
-                st_load(seg + (size_t)local * kStFloats * K, K, r2);
-                step_adj(p, r2, dd, u.y, lam, g_dd, g_ax);
+                st_load(seg + (size_t)local * kStFloats * KL, KL, r2);
+                step_adj(p, r2, dd, u.y, lam, g_dd, g_ax, ln);
             }
             // the steering rate is clamped to +/- its limit before use
-            p.grad[((size_t)k * K + j) * 2] = inside ? g_dd : 0.f;
-            p.grad[((size_t)k * K + j) * 2 + 1] = g_ax;
+            if (ln.q == 0) {
+                p.grad[((size_t)k * K + j) * 2] = inside ? g_dd : 0.f;
+                p.grad[((size_t)k * K + j) * 2 + 1] = g_ax;
+            }
         }
         (void)n_steps;
     }
@@ -597,7 +637,8 @@ __global__ void __launch_bounds__(32) grad_kernel(const __grid_constant__ GradPa
 
 cudaError_t launch_grad(const GradParams &p, cudaStream_t stream)
 {
-    grad_kernel<<<(unsigned)((p.K + 31) / 32), 32, 0, stream>>>(p);
+    const size_t threads = (size_t)p.K * kGradLanes;
+    grad_kernel<<<(unsigned)((threads + 63) / 64), 64, 0, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,9 @@
 
 namespace atp {
 
+// threads per candidate in the adjoint (one wheel each)
+constexpr int kGradLanes = 4;
+
 struct GradParams {
     Veh V;
     Cost C;
@@ -18,8 +21,8 @@ struct GradParams {
     float h;
     float *cost;              // [K]
     float *grad;              // [H][K][2]
-    float *ckpt_buf;          // [ceil(H / ckpt)][20][K]
-    float *seg_buf;           // [ckpt * n_sub][20][K]
+    float *ckpt_buf;          // [ceil(H / ckpt)][20][K * kGradLanes]
+    float *seg_buf;           // [ckpt * n_sub][20][K * kGradLanes]
 };
 
 cudaError_t launch_grad(const GradParams &p, cudaStream_t stream);

@@ -689,8 +689,9 @@ extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *co
     if (ckpt < 1) return fail(ctx, ATP_ERR_INVALID, "ckpt must be >= 1 (0 selects 10)");
     if (ckpt > H) ckpt = H;
     const size_t n_seg = (size_t)(H + ckpt - 1) / ckpt;
-    const size_t ck_bytes = align_up(n_seg * 20 * (size_t)K * sizeof(float));
-    const size_t seg_bytes = align_up((size_t)ckpt * ns * 20 * (size_t)K * sizeof(float));
+    const size_t KL = (size_t)K * atp::kGradLanes;      // every lane keeps its own states
+    const size_t ck_bytes = align_up(n_seg * 20 * KL * sizeof(float));
+    const size_t seg_bytes = align_up((size_t)ckpt * ns * 20 * KL * sizeof(float));
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
     if ((rc = ensure_scratch_bytes(ctx, ck_bytes + seg_bytes)) != ATP_OK) return rc;
