@@ -2,10 +2,14 @@
 // (arxiv 2603.20525, Sec. IV-A..IV-D) for sm_103a.
 //
 // Design
-//   * One thread per candidate.  Its state stays in registers for the whole
-//     horizon; per Euler step the only memory traffic is 16 terrain texels
-//     (four bilinear lookups of one float4 per corner) through the read-only
-//     path, which the L1 and the 126 MB L2 serve for every terrain size used.
+//   * One, two or four threads per candidate (by batch size): a quad runs one
+//     wheel per lane and a pair one axle per lane, repeating the body
+//     arithmetic on every lane, so that small batches still give each SM
+//     sub-partition several warps.  The state stays in registers for the
+//     whole horizon; per Euler step the only memory traffic is 16 terrain
+//     texels (four bilinear lookups of one float4 per corner) through the
+//     read-only path, which the L1 and the 126 MB L2 serve for every terrain
+//     size used.
 //   * Controls are time-major float2 [H][N]: a warp reads one coalesced 256 B
 //     line per control step.
 //   * The reduction is fused into the tail: a warp-shuffle min of a packed

@@ -2,9 +2,10 @@
 // vehicle of arxiv 2603.20525, Sec. IV-A, with the sigmoid tire of Sec. III-A,
 // the energy stability margin of Sec. IV-B and the running cost of Sec. IV-C.
 //
-// One thread owns one candidate: its state lives in registers for the whole
-// horizon, so a rollout step reads memory only for the four bilinear terrain
-// lookups (16 texels).
+// A candidate's state lives in registers for the whole horizon (in one
+// thread, or repeated in the two or four threads that share its wheels), so a
+// rollout step reads memory only for the four bilinear terrain lookups (16
+// texels).
 //
 // Precision.  The arithmetic is FP32, compiled without implicit FMA
 // contraction: every fused multiply-add is written as fmaf, so the rounding
