@@ -85,19 +85,12 @@ __device__ __forceinline__ int axis_c(int ic, float fc, float o, float inv_cell,
 {
     const float u = fmaf(o, inv_cell, fc);
     const float fl = floorf(u);
-    int i = ic + (int)fmaxf(fminf(fl, 4194304.f), -4194304.f);
-    a = u - fl;
-    clamped = false;
-    if (i < 0) {
-        i = 0;
-        a = 0.f;
-        clamped = true;
-    } else if (i >= n - 1) {
-        i = n - 2;
-        a = 1.f;
-        clamped = true;
-    }
-    return i;
+    const int i = ic + (int)fmaxf(fminf(fl, 4194304.f), -4194304.f);
+    const float w = u - fl;
+    const bool below = i < 0, above = i >= n - 1;
+    clamped = below || above;
+    a = below ? 0.f : (above ? 1.f : w);
+    return below ? 0 : (above ? n - 2 : i);
 }
 
 // every intermediate of one wheel that its adjoint needs

@@ -45,11 +45,10 @@ struct PlanParams {
 
 constexpr int kPlanBlock = 64;
 // Threads per candidate by batch size, from a sweep of the three layouts on
-// a GB300 (scaled workload, H = 100, 4 Euler steps per control step): four
-// lanes (one wheel each) are fastest up to 16384 candidates (at 16384 by 2 %
-// over two when L2 starts cold), two (one axle each) at 24576, one from
-// 32768 on.
-constexpr int kLanes4MaxN = 16384;
+// a GB300 (scaled workload, H = 100, 4 Euler steps per control step, L2
+// flushed before each plan): four lanes (one wheel each) are fastest up to
+// 12288 candidates, two (one axle each) at 16384 and 24576, one from 32768 on.
+constexpr int kLanes4MaxN = 12288;
 constexpr int kLanes2MaxN = 28672;
 
 // threads per candidate: `forced` (1, 2 or 4) if set, else by batch size

@@ -114,22 +114,19 @@ __device__ __forceinline__ void cell_split(float hi, float lo, float inv_cell, i
 // One axis of a wheel lookup: CoM cell (ic, fc) plus the wheel's offset `o`
 // metres; returns the clamped cell index in [0, n-2] and the weight in [0, 1]
 // (queries clamped to the map, reading Q10).
+// Written with selects rather than branches: the four wheels' lookups then
+// form one basic block that the compiler can interleave (measured on the
+// GB300: 9 % off a full-GPU plan, 3 to 10 % off the smaller ones).
 __device__ __forceinline__ int axis(int ic, float fc, float o, float inv_cell, int n, float &a, bool &off)
 {
     const float u = fmaf(o, inv_cell, fc);
     const float fl = floorf(u);
-    int i = ic + (int)fmaxf(fminf(fl, 4194304.f), -4194304.f);
-    a = u - fl;
-    if (i < 0) {
-        off = true;
-        i = 0;
-        a = 0.f;
-    } else if (i >= n - 1) {
-        if (i > n - 1 || a > 0.f) off = true;
-        i = n - 2;
-        a = 1.f;
-    }
-    return i;
+    const int i = ic + (int)fmaxf(fminf(fl, 4194304.f), -4194304.f);
+    const float w = u - fl;
+    const bool below = i < 0, above = i >= n - 1;
+    off = off || below || (above && (i > n - 1 || w > 0.f));
+    a = below ? 0.f : (above ? 1.f : w);
+    return below ? 0 : (above ? n - 2 : i);
 }
 
 __device__ __forceinline__ float lerp2d(float t00, float t10, float t01, float t11, float a, float b)
