@@ -47,8 +47,14 @@ __device__ __forceinline__ float pair_sum(float v, unsigned mask)
 // two lanes give the same bits.  LANES = 4: lane q of the quad runs wheel q
 // (fl, fr, rl, rr).  The body-level arithmetic is repeated bit-identically on
 // every lane of a candidate, so lanes never exchange state, only the five
-// force/moment sums and the costmap sum.
-template <int LANES, bool PER_X0, int TEX>
+// force/moment sums and the costmap sum.  ACC selects the running cost's
+// accumulator: kAccF32, kAccF64, or kAccRuntime (p.acc64 decides; the batch
+// kernel, which would otherwise inline twice as many variants).  A
+// compile-time choice keeps the step loop free of the uniform branch.
+constexpr int kAccF32 = 0, kAccF64 = 1, kAccRuntime = 2;
+
+
+template <int LANES, bool PER_X0, int TEX, int ACC>
 __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, unsigned qmask,
                                             float &J, float &margin, bool &feasible)
 {
@@ -88,7 +94,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
         }
         bool done = false, off = false;
         const float h = p.h;
-        double J64 = 0.0;          // the running cost in FP64 when p.acc64
+        const bool acc64 = ACC == kAccRuntime ? p.acc64 != 0 : ACC == kAccF64;
+        double J64 = 0.0;          // the running cost in FP64 when acc64
         float Ufrozen = 0.f;
 
         for (int k = 0; k < p.H; ++k) {
@@ -109,14 +116,20 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 const float U = esm(V, ph, sph, cph, cth);
                 margin = fminf(margin, U);
                 sm = fminf(sm, U);
-                // goal test before the step (Sec. IV-C, reading Q4)
+                // goal test before the step (Sec. IV-C, reading Q4).  One and
+                // four lanes skip the step at the goal; two lanes compute it
+                // and discard it (`keep`), which keeps the loop body one basic
+                // block and measured faster there, slower with one or four
                 const float gdx = (x - Cc.gx_hi) + (xl - Cc.gx_lo);
                 const float gdy = (y - Cc.gy_hi) + (yl - Cc.gy_lo);
-                if (fmaf(gdx, gdx, gdy * gdy) <= Cc.goal_r2) {
+                const bool reached = fmaf(gdx, gdx, gdy * gdy) <= Cc.goal_r2;
+                if (LANES != 2 && reached) {
                     done = true;
                     Ufrozen = U;
                     continue;
                 }
+                const bool keep = LANES == 2 && reached;
+                bool offs = false;     // a wheel of this step off the map
                 // 3-2-1 rotation, body -> world (Sec. IV-A)
                 Body B;
                 float *R = B.R;
@@ -143,10 +156,10 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 // longitudinal constraint force enters My only
                 float FyB, FzB, Mx, My, Mz, csum;
                 if (LANES == 1) {
-                    const WheelOut fl = wheel<TEX>(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, off);
-                    const WheelOut fr = wheel<TEX>(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, off);
-                    const WheelOut rl = wheel<TEX>(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, off);
-                    const WheelOut rr = wheel<TEX>(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, off);
+                    const WheelOut fl = wheel<TEX>(V, T, B, V.Lf, V.he, V.kf, V.bf, V.Fsf, d, offs);
+                    const WheelOut fr = wheel<TEX>(V, T, B, V.Lf, -V.he, V.kf, V.bf, V.Fsf, d, offs);
+                    const WheelOut rl = wheel<TEX>(V, T, B, -V.Lr, V.he, V.kr, V.br, V.Fsr, 0.f, offs);
+                    const WheelOut rr = wheel<TEX>(V, T, B, -V.Lr, -V.he, V.kr, V.br, V.Fsr, 0.f, offs);
                     const float Fyf = (fl.Fy + fr.Fy) * cd;
                     const float Fyr = rl.Fy + rr.Fy;
                     FyB = Fyf + Fyr;
@@ -157,8 +170,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     csum = (fl.cost + fr.cost) + (rl.cost + rr.cost);
                 } else if (LANES == 2) {
                     // this lane's axle: left and right wheel
-                    const WheelOut l = wheel<TEX>(V, T, B, wrx, V.he, wk, wb, wFs, front ? d : 0.f, off);
-                    const WheelOut r = wheel<TEX>(V, T, B, wrx, -V.he, wk, wb, wFs, front ? d : 0.f, off);
+                    const WheelOut l = wheel<TEX>(V, T, B, wrx, V.he, wk, wb, wFs, front ? d : 0.f, offs);
+                    const WheelOut r = wheel<TEX>(V, T, B, wrx, -V.he, wk, wb, wFs, front ? d : 0.f, offs);
                     const float fy = front ? (l.Fy + r.Fy) * cd : l.Fy + r.Fy;
                     const float fz = l.Fz + r.Fz;
                     FyB = pair_sum(fy, qmask);
@@ -168,7 +181,7 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     Mz = pair_sum(wrx * fy, qmask);
                     csum = T.has_cm ? pair_sum(l.cost + r.cost, qmask) : 0.f;
                 } else {
-                    const WheelOut w = wheel<TEX>(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, off);
+                    const WheelOut w = wheel<TEX>(V, T, B, wrx, wry, wk, wb, wFs, front ? d : 0.f, offs);
                     const float fy = front ? w.Fy * cd : w.Fy;
                     FyB = quad_sum(fy, qmask);
                     FzB = quad_sum(w.Fz, qmask);
@@ -182,8 +195,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 // running cost L = L_0 + L_soft (Sec. IV-C), left Riemann sum
                 const float soft = fmaxf(fmaf(-U, Cc.inv_eps, 1.f), 0.f);
                 const float L = fmaf(Cc.sigma * soft, soft, fmaf(Cc.wc * dd, dd, Cc.wt)) + csum;
-                if (p.acc64) J64 += (double)(h * L);
-                else J = fmaf(h, L, J);
+                if (acc64) J64 += keep ? 0.0 : (double)(h * L);
+                else J = keep ? J : fmaf(h, L, J);
                 // state derivative A(xi) + B zeta (Sec. IV-A)
                 const float ic = rcp(cth);
                 const float wsc = fmaf(sph, wy, cph * wz);
@@ -198,20 +211,29 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 const float dwx = fmaf(V.dJyz * wy, wz, Mx) * V.invJxx;
                 const float dwy = fmaf(-V.dJxz * wx, wz, My) * V.invJyy;
                 const float dwz = fmaf(V.dJxy * wx, wy, Mz) * V.invJzz;
-                // forward Euler (Sec. IV-D), steering angle clamped (reading Q5)
-                acc2(x, xl, h * dx);
-                acc2(y, yl, h * dy);
-                acc2(z, zl, h * dz);
-                acc2(psi, psil, h * dpsi);
-                th = fmaf(h, dth, th);
-                ph = fmaf(h, dph, ph);
-                acc2(vx, vxl, h * ax);
-                acc2(vy, vyl, h * dvy);
-                acc2(vz, vzl, h * dvz);
-                wx = fmaf(h, dwx, wx);
-                wy = fmaf(h, dwy, wy);
-                wz = fmaf(h, dwz, wz);
-                d = clamp_keep_nan(fmaf(h, dd, d), -V.dmax, V.dmax);
+                // forward Euler (Sec. IV-D), steering angle clamped (reading Q5),
+                // committed unless the step is discarded at the goal
+                float nx = x, nxl = xl, ny = y, nyl = yl, nz = z, nzl = zl, np_ = psi, npl = psil;
+                float nvx = vx, nvxl = vxl, nvy = vy, nvyl = vyl, nvz = vz, nvzl = vzl;
+                acc2(nx, nxl, h * dx);
+                acc2(ny, nyl, h * dy);
+                acc2(nz, nzl, h * dz);
+                acc2(np_, npl, h * dpsi);
+                acc2(nvx, nvxl, h * ax);
+                acc2(nvy, nvyl, h * dvy);
+                acc2(nvz, nvzl, h * dvz);
+                const float nth = fmaf(h, dth, th), nph = fmaf(h, dph, ph);
+                const float nwx = fmaf(h, dwx, wx), nwy = fmaf(h, dwy, wy), nwz = fmaf(h, dwz, wz);
+                const float nd = clamp_keep_nan(fmaf(h, dd, d), -V.dmax, V.dmax);
+                if (!keep) {
+                    x = nx; xl = nxl; y = ny; yl = nyl; z = nz; zl = nzl; psi = np_; psil = npl;
+                    vx = nvx; vxl = nvxl; vy = nvy; vyl = nvyl; vz = nvz; vzl = nvzl;
+                    th = nth; ph = nph; wx = nwx; wy = nwy; wz = nwz; d = nd;
+                    off = off || offs;
+                } else {
+                    done = true;
+                    Ufrozen = U;
+                }
             }
             if (p.step_margin && q == 0) p.step_margin[(size_t)k * p.N + j] = sm;
         }
@@ -234,7 +256,7 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
             const float gdy = (y - Cc.gy_hi) + (yl - Cc.gy_lo);
             const float d2 = fmaf(gdx, gdx, gdy * gdy);
             if (!done && d2 <= Cc.goal_r2) done = true;
-            if (p.acc64) J = (float)(J64 + (double)(Cc.wg * sqrtf(d2)));
+            if (acc64) J = (float)(J64 + (double)(Cc.wg * sqrtf(d2)));
             else J = fmaf(Cc.wg, sqrtf(d2), J);
         }
         // fold the low parts back and leave the terrain frame
@@ -265,7 +287,7 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
 // Register budgets, from A/B runs on the GB300: four lanes run best with
 // ptxas free to use about 104 registers (minimum 1 CTA per SM), one and two
 // lanes with the 128-register cap of 8 resident 64-thread CTAs per SM.
-template <int LANES, bool PER_X0, bool REDUCE, int TEX>
+template <int LANES, bool PER_X0, bool REDUCE, int TEX, int ACC>
 __global__ void __launch_bounds__(kPlanBlock, LANES == 4 ? 1 : 8)
 plan_kernel(const __grid_constant__ PlanParams p)
 {
@@ -277,7 +299,7 @@ plan_kernel(const __grid_constant__ PlanParams p)
                                                         : (0xfu << (threadIdx.x & 28));
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
-    if (live) rollout_one<LANES, PER_X0, TEX>(p, j, q, qmask, J, margin, feasible);
+    if (live) rollout_one<LANES, PER_X0, TEX, ACC>(p, j, q, qmask, J, margin, feasible);
     if (!REDUCE) return;
     plan_tail(p, j, live && q == 0, J, feasible, gridDim.x);
 }
@@ -309,19 +331,19 @@ plan_batch_kernel(const __grid_constant__ BatchParams b)
     if (live) {
         if (four) {
             if (p.tex_format == TEX_F32) {
-                if (p.x0_soa) rollout_one<4, true, TEX_F32>(p, j, q, qmask, J, margin, feasible);
-                else rollout_one<4, false, TEX_F32>(p, j, q, qmask, J, margin, feasible);
+                if (p.x0_soa) rollout_one<4, true, TEX_F32, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
+                else rollout_one<4, false, TEX_F32, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
             } else {
-                if (p.x0_soa) rollout_one<4, true, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
-                else rollout_one<4, false, TEX_BF16>(p, j, q, qmask, J, margin, feasible);
+                if (p.x0_soa) rollout_one<4, true, TEX_BF16, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
+                else rollout_one<4, false, TEX_BF16, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
             }
         } else {
             if (p.tex_format == TEX_F32) {
-                if (p.x0_soa) rollout_one<1, true, TEX_F32>(p, j, 0, 0u, J, margin, feasible);
-                else rollout_one<1, false, TEX_F32>(p, j, 0, 0u, J, margin, feasible);
+                if (p.x0_soa) rollout_one<1, true, TEX_F32, kAccRuntime>(p, j, 0, 0u, J, margin, feasible);
+                else rollout_one<1, false, TEX_F32, kAccRuntime>(p, j, 0, 0u, J, margin, feasible);
             } else {
-                if (p.x0_soa) rollout_one<1, true, TEX_BF16>(p, j, 0, 0u, J, margin, feasible);
-                else rollout_one<1, false, TEX_BF16>(p, j, 0, 0u, J, margin, feasible);
+                if (p.x0_soa) rollout_one<1, true, TEX_BF16, kAccRuntime>(p, j, 0, 0u, J, margin, feasible);
+                else rollout_one<1, false, TEX_BF16, kAccRuntime>(p, j, 0, 0u, J, margin, feasible);
             }
         }
     }
@@ -335,21 +357,28 @@ cudaError_t launch_plan_batch(const BatchParams &b, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <int LANES, int TEX>
-static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t stream)
+template <int LANES, int TEX, int ACC>
+static cudaError_t launch_acc(const PlanParams &p, bool reduce, cudaStream_t stream)
 {
     const dim3 block(kPlanBlock);
     const size_t threads = (size_t)p.N * LANES;
     const dim3 grid((unsigned)((threads + kPlanBlock - 1) / kPlanBlock));
     const bool per = p.x0_soa != nullptr;
     if (reduce) {
-        if (per) plan_kernel<LANES, true, true, TEX><<<grid, block, 0, stream>>>(p);
-        else plan_kernel<LANES, false, true, TEX><<<grid, block, 0, stream>>>(p);
+        if (per) plan_kernel<LANES, true, true, TEX, ACC><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<LANES, false, true, TEX, ACC><<<grid, block, 0, stream>>>(p);
     } else {
-        if (per) plan_kernel<LANES, true, false, TEX><<<grid, block, 0, stream>>>(p);
-        else plan_kernel<LANES, false, false, TEX><<<grid, block, 0, stream>>>(p);
+        if (per) plan_kernel<LANES, true, false, TEX, ACC><<<grid, block, 0, stream>>>(p);
+        else plan_kernel<LANES, false, false, TEX, ACC><<<grid, block, 0, stream>>>(p);
     }
     return cudaGetLastError();
+}
+
+template <int LANES, int TEX>
+static cudaError_t launch_lanes(const PlanParams &p, bool reduce, cudaStream_t stream)
+{
+    return p.acc64 ? launch_acc<LANES, TEX, kAccF64>(p, reduce, stream)
+                   : launch_acc<LANES, TEX, kAccF32>(p, reduce, stream);
 }
 
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream)
