@@ -69,8 +69,12 @@ __device__ __forceinline__ void est_one(const PlanParams &p, int j, float &J, fl
     const float h = p.h;
     const bool cm = T.has_cm != 0;
     double J64 = 0.0;
+    // each interval's control is loaded one interval ahead, so the load's
+    // latency overlaps the Euler steps
+    float2 un = p.H > 0 ? __ldg(p.ctrl + j) : make_float2(0.f, 0.f);
     for (int k = 0; k < p.H; ++k) {
-        const float2 u = __ldg(p.ctrl + (size_t)k * p.N + j);
+        const float2 u = un;
+        if (k + 1 < p.H) un = __ldg(p.ctrl + (size_t)(k + 1) * p.N + j);
         const float dd = clamp_keep_nan(u.x, -V.ddmax, V.ddmax);
         const float ax = u.y;
         float sm = CUDART_INF_F;

@@ -98,9 +98,16 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
         double J64 = 0.0;          // the running cost in FP64 when acc64
         float Ufrozen = 0.f;
 
+        // four lanes load each interval's control one interval ahead, so the
+        // load's latency overlaps the Euler steps (measured faster there; one
+        // and two lanes run at the 128-register cap, where the two extra live
+        // registers cost more than the latency saved)
+        constexpr bool kPrefetch = LANES == 4;
+        float2 un = kPrefetch && p.H > 0 ? __ldg(p.ctrl + j) : make_float2(0.f, 0.f);
         for (int k = 0; k < p.H; ++k) {
             // zero-order hold; admissible steering rate |delta_dot| <= max
-            const float2 u = __ldg(p.ctrl + (size_t)k * p.N + j);
+            const float2 u = kPrefetch ? un : __ldg(p.ctrl + (size_t)k * p.N + j);
+            if (kPrefetch && k + 1 < p.H) un = __ldg(p.ctrl + (size_t)(k + 1) * p.N + j);
             const float dd = clamp_keep_nan(u.x, -V.ddmax, V.ddmax);
             const float ax = u.y;
             float sm = CUDART_INF_F;
