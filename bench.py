@@ -219,9 +219,23 @@ def cpu_baseline(w, budget_s=10.0):
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 200:
             break
-    return {"value": n * w.N * w.H / el, "unit": "rollout-steps/s", "cores": os.cpu_count() or 1,
-            "kind": "oracle",
-            "sample": f"{n} whole plans of the workload ({n * w.N} candidates, {el:.1f} s), FP64"}
+    out = {"value": n * w.N * w.H / el, "unit": "rollout-steps/s", "cores": os.cpu_count() or 1,
+           "kind": "oracle",
+           "sample": f"{n} whole plans of the workload ({n * w.N} candidates, {el:.1f} s), FP64"}
+    # the same oracle on one thread, over the first 1024 candidates
+    m = min(w.N, 1024)
+    x0 = w.x0[:m] if w.x0.ndim == 2 else w.x0
+    ctrl = np.ascontiguousarray(w.ctrl[:, :m])
+    n1, t0 = 0, time.perf_counter()
+    while True:
+        oracle.plan(w.vehicle, w.cost, t, x0, ctrl, w.dt, w.n_sub, nthreads=1)
+        n1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= budget_s / 2 or n1 >= 200:
+            break
+    out["single_thread"] = {"value": n1 * m * w.H / el1, "unit": "rollout-steps/s", "cores": 1,
+                            "sample": f"{n1} plans of the first {m} candidates ({el1:.1f} s), FP64"}
+    return out
 
 
 def run_paper_config(ctx, dev, stream, flush, steps=10, warmup=3):

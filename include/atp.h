@@ -289,11 +289,13 @@ int atp_sample(atp_ctx *ctx, const float *prev_best_dev, int H_prev, int shift, 
                float *ctrl_dev, void *stream);
 
 /* Diagnostic: evaluates the library's own FP32 elementary functions next to
- * CUDA's on n input pairs (a_i, b_i), writing 10 floats per pair to out_dev:
+ * CUDA's on n input pairs (a_i, b_i), writing 14 floats per pair to out_dev:
  * [sin a, cos a] (library), [sinf a, cosf a] (CUDA), atan2(a, b) (library),
  * atan2f(a, b) (CUDA), 1/b (library reciprocal), 1.0f/b (IEEE division),
- * 1/sqrt(b) (library), rsqrtf(b) (CUDA).  All pointers are device memory of
- * n (a, b) and 10 n (out) floats. */
+ * 1/sqrt(b) (library), rsqrtf(b) (CUDA), then a b + b by the packed
+ * two-wide FMA and by the scalar one, and b - a by the packed two-wide
+ * subtraction and by the scalar one.  All pointers are device memory of n
+ * (a, b) and 14 n (out) floats. */
 int atp_math_check(const float *a_dev, const float *b_dev, int n, float *out_dev, void *stream);
 
 /* ---- The planar model (App. "Extended Single-Track Vehicle Dynamics

@@ -101,4 +101,39 @@ __device__ __forceinline__ float atan2_r(float y, float x)
     return (x != x || y != y) ? x + y : t;
 }
 
+// Packed two-wide FP32 (fma.rn.f32x2, sub.rn.f32x2; Blackwell): each half is
+// the round-to-nearest IEEE operation of its scalar form, subnormals kept, so
+// the results are the scalar code's bits while one instruction issues both
+// halves.  The rollout is issue-bound once the batch fills the GPU, and the
+// FMA pipe runs a packed instruction at half rate, so packing pays where
+// pairs are already adjacent (a texel's (h, f_x) and (f_y, c) halves) or
+// share an operand.  Only fused multiply-adds and differences are packed: a
+// packed multiply feeding a packed add is fused into one rounding by the
+// compiler despite the explicit rounding mode (measured on the GB300 in every
+// case where the two differ), so the scalar code's separate multiply and add
+// stay scalar.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+
 }  // namespace atp

@@ -1,6 +1,7 @@
 // math_check.cu - evaluates the rollout's own elementary functions
 // (fastmath.cuh) next to CUDA's library functions on the same inputs, so that
-// their error can be bounded on the GPU itself.
+// their error can be bounded on the GPU itself, and the packed two-wide FP32
+// operations next to their scalar forms.
 #include "atp.h"
 #include "fastmath.cuh"
 
@@ -15,7 +16,7 @@ __global__ void math_check_kernel(const float *__restrict__ a, const float *__re
     float s, c, s_ref, c_ref;
     sincos_r(x, s, c);
     sincosf(x, &s_ref, &c_ref);
-    float *o = out + (size_t)10 * i;
+    float *o = out + (size_t)14 * i;
     o[0] = s;
     o[1] = c;
     o[2] = s_ref;
@@ -26,6 +27,11 @@ __global__ void math_check_kernel(const float *__restrict__ a, const float *__re
     o[7] = 1.0f / y;
     o[8] = rsq(y);
     o[9] = rsqrtf(y);
+    // packed two-wide forms next to their scalar forms
+    o[10] = fma2(make_float2(x, y), make_float2(y, x), make_float2(y, x)).x;
+    o[11] = fmaf(x, y, y);
+    o[12] = sub2(make_float2(x, y), make_float2(y, x)).y;
+    o[13] = __fsub_rn(y, x);
 }
 
 }  // namespace atp

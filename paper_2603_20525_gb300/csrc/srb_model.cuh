@@ -135,16 +135,24 @@ __device__ __forceinline__ float lerp2d(float t00, float t10, float t01, float t
     return fmaf(b, hi - lo, lo);
 }
 
+// lerp2d on two channels at once, bit for bit the same
+__device__ __forceinline__ float2 lerp2d2(float2 t00, float2 t10, float2 t01, float2 t11, float2 a,
+                                          float2 b)
+{
+    const float2 lo = fma2(a, sub2(t10, t00), t00), hi = fma2(a, sub2(t11, t01), t01);
+    return fma2(b, sub2(hi, lo), lo);
+}
+
 // bilinear height, slopes and (when the terrain has a costmap) cost
 __device__ __forceinline__ float4 lerp4(float4 t00, float4 t10, float4 t01, float4 t11, float a, float b,
                                         bool cm)
 {
-    float4 o;
-    o.x = lerp2d(t00.x, t10.x, t01.x, t11.x, a, b);
-    o.y = lerp2d(t00.y, t10.y, t01.y, t11.y, a, b);
-    o.z = lerp2d(t00.z, t10.z, t01.z, t11.z, a, b);
-    o.w = cm ? lerp2d(t00.w, t10.w, t01.w, t11.w, a, b) : 0.f;
-    return o;
+    const float2 a2 = splat2(a), b2 = splat2(b);
+    const float2 xy = lerp2d2(make_float2(t00.x, t00.y), make_float2(t10.x, t10.y),
+                              make_float2(t01.x, t01.y), make_float2(t11.x, t11.y), a2, b2);
+    const float2 zw = lerp2d2(make_float2(t00.z, t00.w), make_float2(t10.z, t10.w),
+                              make_float2(t01.z, t01.w), make_float2(t11.z, t11.w), a2, b2);
+    return make_float4(xy.x, xy.y, zw.x, cm ? zw.y : 0.f);
 }
 
 // height of a block's plane (c0, cx, cy) at node (i, j): c0 + cx (i mod 8) +
@@ -205,8 +213,10 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
 {
     const float *R = B.R;
     // offset of the contact point from the CoM in W: R (rx, ry, -(h+R))
-    const float ox = fmaf(rx, R[0], fmaf(ry, R[1], -V.hR * R[2]));
-    const float oy = fmaf(rx, R[3], fmaf(ry, R[4], -V.hR * R[5]));
+    const float2 oxy = fma2(splat2(rx), make_float2(R[0], R[3]),
+                            fma2(splat2(ry), make_float2(R[1], R[4]),
+                                 make_float2(-V.hR * R[2], -V.hR * R[5])));
+    const float ox = oxy.x, oy = oxy.y;
     const float oz = fmaf(rx, R[6], fmaf(ry, R[7], -V.hR * R[8]));
     // body velocity of the contact point: v + w x rho
     const float vix = fmaf(-B.wz, ry, fmaf(-B.wy, V.hR, B.vx));
@@ -218,8 +228,9 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     const int j = axis(B.icy, B.fcy, oy, T.inv_cell, T.ny, bb, off);
     const float4 t = bilerp<TEX>(T, i, j, a, bb);
     // tau in B = R^T (-f_x, -f_y, 1)
-    const float tx = fmaf(-R[3], t.z, fmaf(-R[0], t.y, R[6]));
-    const float ty = fmaf(-R[4], t.z, fmaf(-R[1], t.y, R[7]));
+    const float2 txy = fma2(make_float2(-R[3], -R[4]), splat2(t.z),
+                            fma2(make_float2(-R[0], -R[1]), splat2(t.y), make_float2(R[6], R[7])));
+    const float tx = txy.x, ty = txy.y;
     const float tz = fmaf(-R[5], t.z, fmaf(-R[2], t.y, R[8]));
     const float itz = rcp(tz);
     // P_z - f with the compensated CoM height

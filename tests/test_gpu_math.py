@@ -2,7 +2,8 @@
 reduction and Taylor series, atan2 by octant reduction and a fitted
 polynomial, the MUFU reciprocal and reciprocal square root) against CUDA's
 library functions and an
-FP64 reference, on the GPU through atp_math_check."""
+FP64 reference, and the packed two-wide FP32 operations against their scalar
+forms, on the GPU through atp_math_check."""
 import ctypes as C
 
 import numpy as np
@@ -17,7 +18,7 @@ def run(a, b):
     L = atp.load()
     ad = torch.as_tensor(np.asarray(a, np.float32)).cuda()
     bd = torch.as_tensor(np.asarray(b, np.float32)).cuda()
-    out = torch.empty((len(a), 10), dtype=torch.float32, device="cuda")
+    out = torch.empty((len(a), 14), dtype=torch.float32, device="cuda")
     assert L.atp_math_check(C.c_void_p(ad.data_ptr()), C.c_void_p(bd.data_ptr()), len(a),
                             C.c_void_p(out.data_ptr()), None) == 0
     torch.cuda.synchronize()
@@ -83,3 +84,28 @@ def test_reciprocal_sqrt_within_two_ulp():
     rel_cuda = np.abs(o[:, 9] - ref) / ref
     print("rsqrt max rel error: library", rel.max(), "CUDA", rel_cuda.max())
     assert rel.max() <= 2.4e-7
+
+
+def test_packed_fp32_matches_scalar_bits():
+    """The packed two-wide FMA and subtraction give the scalar operations'
+    bits, over every magnitude including subnormal operands and results."""
+    rng = np.random.default_rng(5)
+    n = 400000
+    a = (rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-44, 30, n)).astype(np.float32)
+    b = (rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-44, 30, n)).astype(np.float32)
+    tiny = np.float32(1.4e-45)
+    extra_a = np.array([0.0, -0.0, tiny, -tiny, 1e-39, 3e-39, 1.0, np.inf, np.nan], np.float32)
+    extra_b = np.array([-0.0, 0.0, tiny, tiny, -5e-39, 2e-39, -1.0, 1.0, 2.0], np.float32)
+    a = np.concatenate([a, extra_a, rng.uniform(-1, 1, 100000).astype(np.float32)])
+    b = np.concatenate([b, extra_b, rng.uniform(-1, 1, 100000).astype(np.float32)])
+    from paper_2603_20525_gb300 import atp
+    L = atp.load()
+    ad = torch.as_tensor(a).cuda()
+    bd = torch.as_tensor(b).cuda()
+    out = torch.empty((len(a), 14), dtype=torch.float32, device="cuda")
+    assert L.atp_math_check(C.c_void_p(ad.data_ptr()), C.c_void_p(bd.data_ptr()), len(a),
+                            C.c_void_p(out.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(o[:, 10], o[:, 11])
+    assert np.array_equal(o[:, 12], o[:, 13])
