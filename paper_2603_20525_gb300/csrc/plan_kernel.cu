@@ -141,11 +141,20 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 Body B;
                 float *R = B.R;
                 R[0] = cps * cth;
-                R[1] = fmaf(cps * sph, sth, -cph * sps);
-                R[2] = fmaf(cph * cps, sth, sph * sps);
+                if constexpr (LANES == 2) {
+                    // packed pairs, the same bits (see wheel's PAIRED)
+                    const float2 r12 = fma2(make_float2(cps * sph, cph * cps), splat2(sth),
+                                            make_float2(-cph * sps, sph * sps));
+                    const float2 r45 = fma2(make_float2(sph * sps, cph * sps), splat2(sth),
+                                            make_float2(cph * cps, -cps * sph));
+                    R[1] = r12.x; R[2] = r12.y; R[4] = r45.x; R[5] = r45.y;
+                } else {
+                    R[1] = fmaf(cps * sph, sth, -cph * sps);
+                    R[2] = fmaf(cph * cps, sth, sph * sps);
+                    R[4] = fmaf(sph * sps, sth, cph * cps);
+                    R[5] = fmaf(cph * sps, sth, -cps * sph);
+                }
                 R[3] = cth * sps;
-                R[4] = fmaf(sph * sps, sth, cph * cps);
-                R[5] = fmaf(cph * sps, sth, -cps * sph);
                 R[6] = -sth;
                 R[7] = cth * sph;
                 R[8] = cph * cth;
@@ -177,8 +186,9 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     csum = (fl.cost + fr.cost) + (rl.cost + rr.cost);
                 } else if (LANES == 2) {
                     // this lane's axle: left and right wheel
-                    const WheelOut l = wheel<TEX>(V, T, B, wrx, V.he, wk, wb, wFs, front ? d : 0.f, offs);
-                    const WheelOut r = wheel<TEX>(V, T, B, wrx, -V.he, wk, wb, wFs, front ? d : 0.f, offs);
+                    const float di = front ? d : 0.f;
+                    const WheelOut l = wheel<TEX, true>(V, T, B, wrx, V.he, wk, wb, wFs, di, offs);
+                    const WheelOut r = wheel<TEX, true>(V, T, B, wrx, -V.he, wk, wb, wFs, di, offs);
                     const float fy = front ? (l.Fy + r.Fy) * cd : l.Fy + r.Fy;
                     const float fz = l.Fz + r.Fz;
                     FyB = pair_sum(fy, qmask);
@@ -207,8 +217,17 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 // state derivative A(xi) + B zeta (Sec. IV-A)
                 const float ic = rcp(cth);
                 const float wsc = fmaf(sph, wy, cph * wz);
-                const float dx = fmaf(R[2], vz, fmaf(R[1], vy, R[0] * vx));
-                const float dy = fmaf(R[5], vz, fmaf(R[4], vy, R[3] * vx));
+                float dx, dy;
+                if constexpr (LANES == 2) {
+                    const float2 dxy = fma2(make_float2(R[2], R[5]), splat2(vz),
+                                            fma2(make_float2(R[1], R[4]), splat2(vy),
+                                                 make_float2(R[0] * vx, R[3] * vx)));
+                    dx = dxy.x;
+                    dy = dxy.y;
+                } else {
+                    dx = fmaf(R[2], vz, fmaf(R[1], vy, R[0] * vx));
+                    dy = fmaf(R[5], vz, fmaf(R[4], vy, R[3] * vx));
+                }
                 const float dz = fmaf(R[8], vz, fmaf(R[7], vy, R[6] * vx));
                 const float dpsi = wsc * ic;
                 const float dth = fmaf(cph, wy, -sph * wz);

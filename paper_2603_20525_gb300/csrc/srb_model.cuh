@@ -129,6 +129,24 @@ __device__ __forceinline__ int axis(int ic, float fc, float o, float inv_cell, i
     return below ? 0 : (above ? n - 2 : i);
 }
 
+// axis() for both axes of one lookup, with the cell coordinate and fraction
+// of the two taken as pairs; bit for bit the same as two axis() calls
+__device__ __forceinline__ void axis_xy(int icx, int icy, float2 fc, float2 o, float inv_cell, int nx,
+                                        int ny, int &i, int &j, float &a, float &b, bool &off)
+{
+    const float2 u = fma2(o, splat2(inv_cell), fc);
+    const float2 fl = make_float2(floorf(u.x), floorf(u.y));
+    const float2 w = sub2(u, fl);
+    const int ix = icx + (int)fmaxf(fminf(fl.x, 4194304.f), -4194304.f);
+    const int iy = icy + (int)fmaxf(fminf(fl.y, 4194304.f), -4194304.f);
+    const bool bx = ix < 0, ex = ix >= nx - 1, by = iy < 0, ey = iy >= ny - 1;
+    off = off || bx || (ex && (ix > nx - 1 || w.x > 0.f)) || by || (ey && (iy > ny - 1 || w.y > 0.f));
+    a = bx ? 0.f : (ex ? 1.f : w.x);
+    b = by ? 0.f : (ey ? 1.f : w.y);
+    i = bx ? 0 : (ex ? nx - 2 : ix);
+    j = by ? 0 : (ey ? ny - 2 : iy);
+}
+
 __device__ __forceinline__ float lerp2d(float t00, float t10, float t01, float t11, float a, float b)
 {
     const float lo = fmaf(a, t10 - t00, t00), hi = fmaf(a, t11 - t01, t01);
@@ -205,8 +223,10 @@ struct Body {
 // One wheel (Sec. IV-A): contact point P = p + R rho, its body velocity
 // v + w x rho, terrain below it, extension chi and rate against the local
 // slope-normal tau ~ (-f_x, -f_y, 1) (reading Q1), spring and damper with
-// liftoff, slip angle and sigmoid tire force.
-template <int TEX>
+// liftoff, slip angle and sigmoid tire force.  PAIRED takes the lookup's two
+// axes and the suspension rate's inner pair as packed pairs: the same bits,
+// measured faster with two lanes per candidate and slower with one or four.
+template <int TEX, bool PAIRED = false>
 __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const Body &B,
                                           float rx, float ry, float k, float b, float Fs,
                                           float di, bool &off)
@@ -216,7 +236,6 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     const float2 oxy = fma2(splat2(rx), make_float2(R[0], R[3]),
                             fma2(splat2(ry), make_float2(R[1], R[4]),
                                  make_float2(-V.hR * R[2], -V.hR * R[5])));
-    const float ox = oxy.x, oy = oxy.y;
     const float oz = fmaf(rx, R[6], fmaf(ry, R[7], -V.hR * R[8]));
     // body velocity of the contact point: v + w x rho
     const float vix = fmaf(-B.wz, ry, fmaf(-B.wy, V.hR, B.vx));
@@ -224,8 +243,13 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     const float viz = fmaf(-B.wy, rx, fmaf(B.wx, ry, B.vz));
     // terrain below the contact point
     float a, bb;
-    const int i = axis(B.icx, B.fcx, ox, T.inv_cell, T.nx, a, off);
-    const int j = axis(B.icy, B.fcy, oy, T.inv_cell, T.ny, bb, off);
+    int i, j;
+    if constexpr (PAIRED) {
+        axis_xy(B.icx, B.icy, make_float2(B.fcx, B.fcy), oxy, T.inv_cell, T.nx, T.ny, i, j, a, bb, off);
+    } else {
+        i = axis(B.icx, B.fcx, oxy.x, T.inv_cell, T.nx, a, off);
+        j = axis(B.icy, B.fcy, oxy.y, T.inv_cell, T.ny, bb, off);
+    }
     const float4 t = bilerp<TEX>(T, i, j, a, bb);
     // tau in B = R^T (-f_x, -f_y, 1)
     const float2 txy = fma2(make_float2(-R[3], -R[4]), splat2(t.z),
@@ -236,8 +260,13 @@ __device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const 
     // P_z - f with the compensated CoM height
     const float chi = ((B.z_hi - t.x) + (oz + B.z_lo)) * itz;
     // omega x b_z in B is (w_y, -w_x, 0)
-    const float chid =
-        fmaf(tz, viz, fmaf(ty, fmaf(chi, B.wx, viy), tx * fmaf(-chi, B.wy, vix))) * itz;
+    float chid;
+    if constexpr (PAIRED) {
+        const float2 rel = fma2(splat2(chi), make_float2(B.wx, -B.wy), make_float2(viy, vix));
+        chid = fmaf(tz, viz, fmaf(ty, rel.x, tx * rel.y)) * itz;
+    } else {
+        chid = fmaf(tz, viz, fmaf(ty, fmaf(chi, B.wx, viy), tx * fmaf(-chi, B.wy, vix))) * itz;
+    }
     const float Fk = fmaxf(fmaf(-k, chi, Fs), 0.f);
     const float Fz = Fk > 0.f ? fmaxf(fmaf(-b, chid, Fk), 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
     const float alpha = atan2_r(viy, vix) - di;
