@@ -132,3 +132,22 @@ def test_admission_replays_arrival_order_under_backlog():
     for v, rids in order.items():
         assert rids == sorted(rids)
     assert sum(len(r) for r in order.values()) == 400
+
+
+def test_collector_paused_restores_state():
+    import gc
+    assert gc.isenabled()
+    with serve.collector_paused():
+        assert not gc.isenabled()
+    assert gc.isenabled()
+    with pytest.raises(RuntimeError):
+        with serve.collector_paused():
+            raise RuntimeError("loop failed")
+    assert gc.isenabled()
+    gc.disable()
+    try:
+        with serve.collector_paused():
+            assert not gc.isenabled()
+        assert not gc.isenabled()          # a caller's own pause is kept
+    finally:
+        gc.enable()
