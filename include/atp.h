@@ -253,10 +253,13 @@ typedef struct {
 /* Continuous batching: n_req (1..64) independent plans, each with its own
  * vehicle, terrain, candidates, horizon and outputs, in one kernel launch.
  * Each plan's results are bit-identical to a single atp_plan of the same
- * request on a context with the same ATP_OPT_LANES (both choose the threads
- * per candidate by the same rule), alone or in any mix.  The context's scratch grows to the sum of the plans' needs;
- * atp_reserve(ctx, sum of N, max H) pre-sizes it for any batch within those
- * totals.  Validation failures name the offending request in atp_last_error. */
+ * request on a context with the same ATP_OPT_LANES, alone or in any mix: a
+ * plan runs four lanes where atp_plan would, and otherwise one or two, which
+ * give the same bits (two only while the batch's threads stay within what a
+ * two-lane plan alone may use, or when ATP_OPT_LANES forces two).  The
+ * context's scratch grows to the sum of the plans' needs; atp_reserve(ctx,
+ * sum of N, max H) pre-sizes it for any batch within those totals.
+ * Validation failures name the offending request in atp_last_error. */
 int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *stream);
 
 /* Gradient of each candidate's cost with respect to its raw controls: the

@@ -500,8 +500,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
     if (!reqs || n_req < 1 || n_req > atp::kMaxBatch)
         return fail(ctx, ATP_ERR_INVALID, "need 1 <= n_req <= %d requests", atp::kMaxBatch);
     size_t need = 0;
-    long long ctas = 0;
-    int ns[atp::kMaxBatch];
+    long long ctas = 0, threads = 0;
+    int ns[atp::kMaxBatch], lanes[atp::kMaxBatch];
     for (int r = 0; r < n_req; ++r) {
         const atp_plan_request &q = reqs[r];
         int rc = common_checks(ctx, q.veh, q.cost, q.terrain, q.x0 ? &q.x0->x : nullptr, 13, q.x0_dev,
@@ -515,9 +515,24 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
         if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
         need += region_layout((size_t)q.N, (size_t)q.H).total;
-        ctas += ((long long)q.N * (atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1) + atp::kPlanBlock - 1) /
-                atp::kPlanBlock;
+        // four lanes sum in another order, so a plan keeps its own layout's
+        // four; two lanes give one lane's bits and are decided below
+        lanes[r] = atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1;
+        threads += (long long)q.N * lanes[r];
     }
+    // Two lanes pay only while the GPU is mostly empty: a plan that would run
+    // two lanes alone runs them in a batch while the batch's threads stay
+    // within what a two-lane plan alone may use (or when two are forced).
+    for (int r = 0; r < n_req; ++r) {
+        const long long N = reqs[r].N;
+        if (atp::plan_lanes(ctx->lanes, reqs[r].N) == 2 &&
+            (ctx->lanes == 2 || threads + N <= 2LL * atp::kLanes2MaxN)) {
+            lanes[r] = 2;
+            threads += N;
+        }
+    }
+    for (int r = 0; r < n_req; ++r)
+        ctas += ((long long)reqs[r].N * lanes[r] + atp::kPlanBlock - 1) / atp::kPlanBlock;
     if (ctas > 0x7fffffffLL) return fail(ctx, ATP_ERR_UNSUPPORTED, "batch too large");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
@@ -544,8 +559,7 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         p.best_margin = q.best_margin_dev;
         p.scratch = (atp::Scratch *)ctx->scratch + r;
         p.acc64 = ctx->acc64;
-        // two lanes give the same bits as one, so a batch runs them as one
-        p.lanes = atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1;
+        p.lanes = lanes[r];
         region += L.total;
         b.cta_begin[r + 1] = b.cta_begin[r] + (int)(((long long)q.N * p.lanes + atp::kPlanBlock - 1) / atp::kPlanBlock);
     }

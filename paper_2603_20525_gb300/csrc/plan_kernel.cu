@@ -332,10 +332,11 @@ plan_kernel(const __grid_constant__ PlanParams p)
 
 // Continuous batching: one launch over a ragged batch of plans, each with its
 // own vehicle, terrain, horizon, candidates and outputs.  Plan r owns CTAs
-// [cta_begin[r], cta_begin[r+1]) with p.lanes (1 or 4, chosen by the same
-// rule as a single plan) threads per candidate; every candidate runs exactly
-// the code of a single plan, so its results are the same bits alone and in
-// any mix.
+// [cta_begin[r], cta_begin[r+1]) with p.lanes threads per candidate: four
+// where a single plan of its size takes four, else one or two (the same
+// bits; two while the batch leaves the GPU mostly empty).  Every candidate
+// runs exactly the code of a single plan, so its results are the same bits
+// alone and in any mix.
 __global__ void __launch_bounds__(kPlanBlock)
 plan_batch_kernel(const __grid_constant__ BatchParams b)
 {
@@ -348,10 +349,12 @@ plan_batch_kernel(const __grid_constant__ BatchParams b)
     const PlanParams &p = b.req[lo];
     const int tid = ((int)blockIdx.x - b.cta_begin[lo]) * kPlanBlock + (int)threadIdx.x;
     // every thread of a CTA belongs to one plan: the branch is CTA-uniform
-    const bool four = p.lanes == 4;
-    const int j = four ? tid >> 2 : tid, q = four ? tid & 3 : 0;
+    const int lanes = p.lanes;
+    const bool four = lanes == 4, two = lanes == 2;
+    const int j = four ? tid >> 2 : two ? tid >> 1 : tid;
+    const int q = four ? tid & 3 : two ? tid & 1 : 0;
     const bool live = j < p.N;
-    const unsigned qmask = four ? 0xfu << (threadIdx.x & 28) : 0u;
+    const unsigned qmask = four ? 0xfu << (threadIdx.x & 28) : two ? 0x3u << (threadIdx.x & 30) : 0u;
     float J = 0.f, margin = CUDART_INF_F;
     bool feasible = false;
     if (live) {
@@ -362,6 +365,14 @@ plan_batch_kernel(const __grid_constant__ BatchParams b)
             } else {
                 if (p.x0_soa) rollout_one<4, true, TEX_BF16, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
                 else rollout_one<4, false, TEX_BF16, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
+            }
+        } else if (two) {
+            if (p.tex_format == TEX_F32) {
+                if (p.x0_soa) rollout_one<2, true, TEX_F32, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
+                else rollout_one<2, false, TEX_F32, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
+            } else {
+                if (p.x0_soa) rollout_one<2, true, TEX_BF16, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
+                else rollout_one<2, false, TEX_BF16, kAccRuntime>(p, j, q, qmask, J, margin, feasible);
             }
         } else {
             if (p.tex_format == TEX_F32) {

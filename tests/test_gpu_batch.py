@@ -117,6 +117,29 @@ def test_alone_and_in_any_mix_bitwise(ctx):
         same(target["out"], alone)
 
 
+def test_two_lane_plan_alone_and_in_a_full_batch_bitwise(ctx):
+    """A plan that runs two lanes alone (20000 candidates) keeps two lanes in
+    a batch that leaves the GPU mostly empty and runs one lane in a batch of
+    three such plans (60000 threads at one lane each, past a two-lane plan's
+    own 57344); one and two lanes give the same bits, so it matches atp_plan
+    either way."""
+    qs = prepare(ctx, requests_mix())
+    big = next(q for q in qs if q["ctrl"].shape[1] == 20000)
+    assert ctx.plan_lanes(20000) == 2
+    single = fresh_outputs(big)
+    ctx.plan(big["veh"], big["cost"], big["terrain"], big["x0"], big["ctrl"], big["dt"], big["n_sub"],
+             out=single)
+    big["out"] = fresh_outputs(big)
+    ctx.plan_batch([big])
+    torch.cuda.synchronize()
+    same(big["out"], single)
+    trio = [dict(big, out=fresh_outputs(big)) for _ in range(3)]
+    ctx.plan_batch(trio)
+    torch.cuda.synchronize()
+    for q in trio:
+        same(q["out"], single)
+
+
 def test_batched_plan_parity_with_oracle(ctx):
     qs = prepare(ctx, requests_mix())
     for q in qs:

@@ -163,16 +163,24 @@ def test_lanes_option_parity(ctx, lanes):
         ctx.set_option(atp.OPT_LANES, 3)
 
 
-def test_one_and_two_lanes_same_bits(ctx):
+@pytest.mark.parametrize("goal_dx", [None, 8.0])
+def test_one_and_two_lanes_same_bits(ctx, goal_dx):
     """A pair of lanes sums each axle and then the two axles, the order one
-    lane uses, so the two layouts agree bit for bit."""
+    lane uses, so the two layouts agree bit for bit.  With the goal 8 m ahead
+    of the start, over half of the candidates reach it mid-horizon, where two
+    lanes compute the step and discard it and one lane skips it."""
     from paper_2603_20525_gb300 import atp
     w = gen.workload_scaled(3, N=3000, H=30)
+    if goal_dx is not None:
+        w = gen.Workload(w.name, w.terrain, w.vehicle, dict(w.cost, goal_x=10.0 + goal_dx), w.x0,
+                         w.ctrl, w.dt, w.n_sub)
     outs = []
     for lanes in (1, 2):
         ctx.set_option(atp.OPT_LANES, lanes)
         outs.append(gpu_plan(ctx, w))
     ctx.set_option(atp.OPT_LANES, 0)
+    if goal_dx is not None:
+        assert np.count_nonzero(outs[0]["flags"] & 2) > 1000      # ATP_FLAG_DONE
     for k in ("cost", "margin", "flags", "xf", "best_ctrl", "best_margin"):
         assert np.array_equal(outs[0][k], outs[1][k]), k
     assert outs[0]["best_idx"] == outs[1]["best_idx"]
@@ -241,21 +249,30 @@ def test_all_infeasible_and_ties(ctx):
     assert g["best_idx"] not in range(40, 48)
 
 
-def test_goal_truncation_and_offmap(ctx):
-    w = gen.workload_plain(6, N=200, H=40)
-    c = dict(w.cost, goal_x=12.0)            # reached mid-horizon
-    ww = gen.Workload(w.name, w.terrain, w.vehicle, c, w.x0, w.ctrl, w.dt, w.n_sub)
-    g = gpu_plan(ctx, ww)
-    o = oracle_plan(ww)
-    assert np.count_nonzero(o["flags"] & oracle.DONE) > 100
-    check_plan(g, o, ww)
-    # start near the map corner so that candidates leave the map
-    x0 = gen.settled_state(w.terrain, w.vehicle, 2.0, 2.0, math.pi * 1.25, 8.0)
-    ww = gen.Workload(w.name, w.terrain, w.vehicle, w.cost, x0, w.ctrl, w.dt, w.n_sub)
-    g = gpu_plan(ctx, ww)
-    o = oracle_plan(ww)
-    assert np.count_nonzero(o["flags"] & oracle.OFFMAP) > 100
-    check_plan(g, o, ww)
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_goal_truncation_and_offmap(ctx, lanes):
+    """Goal truncation (Q4) and off-map lookups in every thread layout: the
+    layouts handle a candidate at its goal differently (one and four lanes
+    skip the step, two lanes compute and discard it)."""
+    from paper_2603_20525_gb300 import atp
+    ctx.set_option(atp.OPT_LANES, lanes)
+    try:
+        w = gen.workload_plain(6, N=200, H=40)
+        c = dict(w.cost, goal_x=12.0)            # reached mid-horizon
+        ww = gen.Workload(w.name, w.terrain, w.vehicle, c, w.x0, w.ctrl, w.dt, w.n_sub)
+        g = gpu_plan(ctx, ww)
+        o = oracle_plan(ww)
+        assert np.count_nonzero(o["flags"] & oracle.DONE) > 100
+        check_plan(g, o, ww)
+        # start near the map corner so that candidates leave the map
+        x0 = gen.settled_state(w.terrain, w.vehicle, 2.0, 2.0, math.pi * 1.25, 8.0)
+        ww = gen.Workload(w.name, w.terrain, w.vehicle, w.cost, x0, w.ctrl, w.dt, w.n_sub)
+        g = gpu_plan(ctx, ww)
+        o = oracle_plan(ww)
+        assert np.count_nonzero(o["flags"] & oracle.OFFMAP) > 100
+        check_plan(g, o, ww)
+    finally:
+        ctx.set_option(atp.OPT_LANES, 0)
 
 
 def test_nonfinite_controls_are_data(ctx):
