@@ -354,7 +354,10 @@ int atp_lod_smooth(atp_ctx *ctx, const float *heights_dev, int nx, int ny, doubl
  *   kind        int [n_poly], host: 0 obstacle, 1 path boundary
  *   cost_dev    float [ny][nx], device
  *   sdist_dev   float [ny][nx] or NULL: the smallest signed distance
- * 1 <= n_poly <= 256. */
+ * 1 <= n_poly <= 256.  Without sdist_dev, each 16 x 16 tile of nodes skips the
+ * obstacles whose bounding box lies more than 2 eps away from it (their rate
+ * there is exactly zero), which gives the same costmap bits as evaluating
+ * every perimeter; with sdist_dev every perimeter is evaluated at every node. */
 int atp_costmap(atp_ctx *ctx, const double *xy_dev, const int *start, const int *kind, int n_poly,
                 int nx, int ny, double cell, double x0, double y0, double eps, double sigma,
                 float *cost_dev, float *sdist_dev, void *stream);

@@ -2,6 +2,7 @@
 // its scratch, FP64 -> FP32 parameter derivation and kernel launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,6 +25,7 @@ struct atp_ctx {
     void *scratch;            // reduction headers + per-plan candidate buffers
     size_t scratch_bytes;
     atp::BatchParams *batch;  // host staging of one batch's descriptors
+    float4 *cm_box;           // the costmap's per-perimeter reach boxes (device)
 };
 
 namespace {
@@ -324,8 +326,14 @@ int atp_create(atp_ctx **out, int device)
         delete ctx;
         return ATP_ERR_CUDA;
     }
+    if (cudaMalloc(&ctx->cm_box, sizeof(float4) * atp::kCostmapMaxPolys) != cudaSuccess) {
+        delete ctx->batch;
+        delete ctx;
+        return ATP_ERR_NOMEM;
+    }
     int rc = ensure_scratch(ctx, 1, 1);
     if (rc != ATP_OK) {
+        cudaFree(ctx->cm_box);
         delete ctx->batch;
         delete ctx;
         return rc;
@@ -340,6 +348,7 @@ int atp_destroy(atp_ctx *ctx)
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->cm_box) cudaFree(ctx->cm_box);
     delete ctx->batch;
     delete ctx;
     return ATP_OK;
@@ -681,7 +690,13 @@ extern "C" int atp_costmap(atp_ctx *ctx, const double *xy_dev, const int *start,
     p.sigma = (float)sigma;
     p.cost = cost_dev;
     p.sdist = sdist_dev;
-    cudaError_t e = atp::launch_costmap(p, (cudaStream_t)stream);
+    // An obstacle farther than eps from a node adds nothing there; the boxes
+    // are grown by twice that plus a margin for the FP32 distance arithmetic
+    // (a few ulps of the map's extent), so a skipped obstacle's rate is
+    // exactly zero at every node of a tile it misses.
+    const double ext = std::max((double)(nx - 1), (double)(ny - 1)) * cell;
+    const float reach = (float)(2.0 * eps + 1e-3 + 1e-5 * ext);
+    cudaError_t e = atp::launch_costmap(p, ctx->cm_box, reach, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "costmap launch");
     return ATP_OK;
 }

@@ -11,7 +11,8 @@
 //     the signed distance to each obstacle or path-boundary perimeter is turned
 //     into the normalised quadratic soft-constraint cost rate and summed over
 //     the perimeters, so that the rollout only interpolates it.  One thread per
-//     node; the perimeters' edges stream through shared memory in chunks.
+//     node; each 16 x 16 tile streams the edges of the perimeters that can
+//     reach it through shared memory in chunks.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -149,26 +150,87 @@ namespace {
 
 constexpr int kChunk = 256;       // vertices staged per pass, one per thread
 
-__device__ __forceinline__ int poly_of(const CostmapParams &p, int v)
+// Bounding box of perimeter blockIdx.x in the costmap kernel's coordinates,
+// grown by `reach`; one warp per perimeter.
+__global__ void __launch_bounds__(32) costmap_boxes_kernel(const __grid_constant__ CostmapParams p,
+                                                           float4 *box, float reach)
 {
-    int lo = 0, hi = p.n_poly;               // start[lo] <= v < start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (p.start[mid] <= v) lo = mid;
-        else hi = mid;
+    const int q = blockIdx.x;
+    float x0 = CUDART_INF_F, y0 = CUDART_INF_F, x1 = -CUDART_INF_F, y1 = -CUDART_INF_F;
+    for (int v = p.start[q] + (int)threadIdx.x; v < p.start[q + 1]; v += 32) {
+        const float x = (float)(p.xy[2 * v] - p.x0), y = (float)(p.xy[2 * v + 1] - p.y0);
+        x0 = fminf(x0, x);
+        y0 = fminf(y0, y);
+        x1 = fmaxf(x1, x);
+        y1 = fmaxf(y1, y);
     }
-    return lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if (threadIdx.x == 0) box[q] = make_float4(x0 - reach, y0 - reach, x1 + reach, y1 + reach);
 }
 
 __global__ void __launch_bounds__(256) costmap_kernel(const __grid_constant__ CostmapParams p)
 {
     __shared__ float2 s_a[kChunk], s_b[kChunk];
     __shared__ int s_poly[kChunk];
+    __shared__ int s_id[kCostmapMaxPolys];        // the tile's perimeters, in order
+    __shared__ int s_off[kCostmapMaxPolys + 1];   // prefix of their vertex counts
+    __shared__ int s_wn[8], s_wv[8];
     const int i = blockIdx.x * 16 + threadIdx.x;
     const int j = blockIdx.y * 16 + threadIdx.y;
     const int t = threadIdx.y * 16 + threadIdx.x;
     const bool live = i < p.nx && j < p.ny;
     const float px = (float)((double)i * p.cell), py = (float)((double)j * p.cell);
+    // the perimeters that can reach this tile (all of them without boxes),
+    // kept in their order by a block-wide scan over one thread per perimeter
+    bool keep = false;
+    int nv = 0;
+    if (t < p.n_poly) {
+        keep = true;
+        if (p.box && p.kind[t] == 0) {
+            const float tx0 = (float)((double)(blockIdx.x * 16) * p.cell);
+            const float tx1 = (float)((double)(blockIdx.x * 16 + 15) * p.cell);
+            const float ty0 = (float)((double)(blockIdx.y * 16) * p.cell);
+            const float ty1 = (float)((double)(blockIdx.y * 16 + 15) * p.cell);
+            const float4 b = p.box[t];
+            keep = !(b.z < tx0 || b.x > tx1 || b.w < ty0 || b.y > ty1);
+        }
+        nv = keep ? p.start[t + 1] - p.start[t] : 0;
+    }
+    const int lane = t & 31, wid = t >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    int inc = nv;                                  // inclusive scan of vertex counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) {
+        s_wn[wid] = __popc(bal);
+        s_wv[wid] = inc;
+    }
+    __syncthreads();
+    int bn = 0, bv = 0, n_keep = 0, n_vert = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        if (w < wid) {
+            bn += s_wn[w];
+            bv += s_wv[w];
+        }
+        n_keep += s_wn[w];
+        n_vert += s_wv[w];
+    }
+    if (keep) {
+        const int k = bn + __popc(bal & ((1u << lane) - 1u));
+        s_id[k] = t;
+        s_off[k] = bv + inc - nv;
+    }
+    if (t == 0) s_off[n_keep] = n_vert;
     float c = 0.f, smin = CUDART_INF_F;
     int cur = -1;
     float d2 = CUDART_INF_F;
@@ -182,18 +244,25 @@ __global__ void __launch_bounds__(256) costmap_kernel(const __grid_constant__ Co
         if (v > 0.f) c = fmaf(p.sigma * v, v, c);
         smin = fminf(smin, s);
     };
-    for (int c0 = 0; c0 < p.n_vert; c0 += kChunk) {
+    for (int c0 = 0; c0 < n_vert; c0 += kChunk) {
         __syncthreads();
-        const int v = c0 + t;
-        if (v < p.n_vert) {
-            const int q = poly_of(p, v);
+        const int vc = c0 + t;
+        if (vc < n_vert) {
+            int lo = 0, hi = n_keep;               // s_off[lo] <= vc < s_off[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= vc) lo = mid;
+                else hi = mid;
+            }
+            const int q = s_id[lo];
+            const int v = p.start[q] + (vc - s_off[lo]);
             const int nxt = v + 1 < p.start[q + 1] ? v + 1 : p.start[q];
             s_a[t] = make_float2((float)(p.xy[2 * v] - p.x0), (float)(p.xy[2 * v + 1] - p.y0));
             s_b[t] = make_float2((float)(p.xy[2 * nxt] - p.x0), (float)(p.xy[2 * nxt + 1] - p.y0));
             s_poly[t] = q;
         }
         __syncthreads();
-        const int m = min(kChunk, p.n_vert - c0);
+        const int m = min(kChunk, n_vert - c0);
         for (int e = 0; e < m; ++e) {
             const int q = s_poly[e];
             if (q != cur) {
@@ -227,8 +296,16 @@ __global__ void __launch_bounds__(256) costmap_kernel(const __grid_constant__ Co
 
 }  // namespace
 
-cudaError_t launch_costmap(const CostmapParams &p, cudaStream_t stream)
+cudaError_t launch_costmap(CostmapParams p, float4 *box_buf, float reach, cudaStream_t stream)
 {
+    if (p.n_poly < 1 || p.n_poly > kCostmapMaxPolys) return cudaErrorInvalidValue;
+    p.box = nullptr;
+    if (box_buf && !p.sdist) {
+        costmap_boxes_kernel<<<(unsigned)p.n_poly, 32, 0, stream>>>(p, box_buf, reach);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        p.box = box_buf;
+    }
     const dim3 grid((unsigned)((p.nx + 15) / 16), (unsigned)((p.ny + 15) / 16));
     costmap_kernel<<<grid, dim3(16, 16), 0, stream>>>(p);
     return cudaGetLastError();

@@ -35,8 +35,16 @@ struct CostmapParams {
     float inv_eps, sigma;
     float *cost;              // [ny][nx]
     float *sdist;             // [ny][nx] or nullptr: smallest signed distance
+    const float4 *box;        // [n_poly] reach boxes (set by launch_costmap) or nullptr
 };
 
-cudaError_t launch_costmap(const CostmapParams &p, cudaStream_t stream);
+// With box_buf (device, kCostmapMaxPolys float4) and no sdist output, a first
+// kernel writes each perimeter's bounding box grown by `reach` metres and the
+// costmap kernel skips, per 16 x 16 tile of nodes, every obstacle whose grown
+// box misses the tile: beyond `reach` (at least twice eps) its cost rate is
+// exactly zero, so the costmap keeps its bits.  Path boundaries are never
+// skipped (their cost lies outside them), nor is anything when sdist is
+// wanted (the smallest distance needs every perimeter).
+cudaError_t launch_costmap(CostmapParams p, float4 *box_buf, float reach, cudaStream_t stream);
 
 }  // namespace atp

@@ -96,6 +96,50 @@ def test_costmap_matches_oracle(ctx, which):
     b = band(polys, (t.ny, t.nx), t.cell, t.x0, t.y0, delta)
     assert np.all(np.abs(cm - oc) <= b + 8 * U * oc + 1e-30)
     assert np.count_nonzero(oc > 0) > 100              # the obstacles cost something
+    # without the distances, tiles skip the obstacles out of their reach:
+    # the same bits
+    cm2 = ctx.costmap(polys, t.nx, t.ny, t.cell, t.x0, t.y0)
+    torch.cuda.synchronize()
+    assert np.array_equal(cm2.cpu().numpy().astype(np.float64), cm)
+
+
+def scattered(t, seed, n, r_lo, r_hi, on_tile_edges=False):
+    """n small convex obstacles over the whole map, optionally centred on the
+    corners of the costmap kernel's 16 x 16-node tiles."""
+    rng = np.random.default_rng(seed)
+    ext_x, ext_y = (t.nx - 1) * t.cell, (t.ny - 1) * t.cell
+    out = []
+    for _ in range(n):
+        if on_tile_edges:
+            cx = t.x0 + 16 * t.cell * rng.integers(1, max(2, t.nx // 16))
+            cy = t.y0 + 16 * t.cell * rng.integers(1, max(2, t.ny // 16))
+        else:
+            cx, cy = t.x0 + rng.uniform(0, ext_x), t.y0 + rng.uniform(0, ext_y)
+        k = int(rng.integers(3, 10))
+        ang = np.sort(rng.uniform(0, 2 * np.pi, k))
+        r = rng.uniform(r_lo, r_hi)
+        out.append((np.stack([cx + r * np.cos(ang), cy + r * np.sin(ang)], 1), 0))
+    return out
+
+
+@pytest.mark.parametrize("eps", [0.02, 0.25, 3.0])
+@pytest.mark.parametrize("edges", [False, True])
+def test_costmap_tile_skipping_keeps_the_bits(ctx, eps, edges):
+    """Obstacles skipped per tile add exactly nothing: the costmap without
+    distances (tiles skip obstacles beyond reach) equals the one with them
+    (every perimeter at every node) bit for bit, for obstacles anywhere, on
+    tile corners, larger than a tile, beside and across the path boundary,
+    on a ragged map."""
+    t = gen.terrain_plain(2)
+    polys = scattered(t, 7, 60, 0.05, 0.8, edges) + scattered(t, 8, 4, 2.0, 6.0)
+    polys = polys[:30] + gen.obstacles(t, 5, n=0) + polys[30:]        # boundary mid-list
+    nx, ny = t.nx - 5, t.ny - 11
+    full, _ = ctx.costmap(polys, nx, ny, t.cell, t.x0, t.y0, eps=eps, want_sdist=True)
+    skip = ctx.costmap(polys, nx, ny, t.cell, t.x0, t.y0, eps=eps)
+    torch.cuda.synchronize()
+    full, skip = full.cpu().numpy(), skip.cpu().numpy()
+    assert np.count_nonzero(full > 0) > 200
+    assert np.array_equal(full.view(np.uint32), skip.view(np.uint32))
 
 
 def test_costmap_feeds_a_plan(ctx):
