@@ -22,8 +22,11 @@ namespace atp {
 
 namespace {
 
-constexpr int kRowTile = 256;     // outputs per row-pass CTA
+constexpr int kRowThreads = 256;  // row-pass CTA
+constexpr int kRowOut = 4;        // consecutive outputs per row-pass thread
+constexpr int kRowTile = kRowThreads * kRowOut;   // outputs per row-pass CTA
 constexpr int kColTile = 64;      // rows per column-pass CTA (32 columns wide)
+constexpr int kColOut = 8;        // consecutive rows per column-pass thread
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -61,54 +64,103 @@ __device__ void gauss_weights(float *w, int r, float inv2s2)
     __syncthreads();
 }
 
-// out[j][i] = sum_k w[k] in[j][clamp(i + k - r)]
-__global__ void __launch_bounds__(kRowTile) lod_rows_kernel(LodParams p)
+// out[j][i] = sum_k w[k] in[j][clamp(i + k - r)], each sum over k in order.
+// Thread t makes outputs 4t .. 4t+3 of the CTA's 1024 from a window of eight
+// tile values refilled by one 16-byte shared load per four taps.
+__global__ void __launch_bounds__(kRowThreads) lod_rows_kernel(LodParams p)
 {
-    extern __shared__ float sm[];
-    float *w = sm;                           // 2r + 1
-    float *tile = sm + 2 * p.r + 1;          // kRowTile + 2r
+    extern __shared__ __align__(16) float sm[];         // the tile is read as float4
+    float *w = sm;                                      // 2r + 1, padded to 4
+    float *tile = sm + ((2 * p.r + 1 + 3) & ~3);        // kRowTile + 2r + 8
     gauss_weights(w, p.r, p.inv2s2);
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * kRowTile;
     const float *row = p.in + (size_t)j * p.nx;
-    for (int t = threadIdx.x; t < kRowTile + 2 * p.r; t += kRowTile)
+    const int n_tile = kRowTile + 2 * p.r + 8;
+    for (int t = threadIdx.x; t < n_tile; t += kRowThreads)
         tile[t] = __ldg(row + clampi(i0 - p.r + t, 0, p.nx - 1));
     __syncthreads();
-    const int i = i0 + threadIdx.x;
-    if (i >= p.nx) return;
-    float acc = 0.f;
-    for (int k = 0; k <= 2 * p.r; ++k) acc = fmaf(w[k], tile[threadIdx.x + k], acc);
-    p.out[(size_t)j * p.nx + i] = acc;
+    const int ib = i0 + kRowOut * threadIdx.x;
+    if (ib >= p.nx) return;
+    const float4 *t4 = reinterpret_cast<const float4 *>(tile) + threadIdx.x;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    float4 lo = t4[0];
+    const int n = 2 * p.r + 1;
+    for (int k0 = 0; k0 < n; k0 += 4) {
+        const float4 hi = t4[(k0 >> 2) + 1];
+        const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (k0 + e < n) {
+                const float wk = w[k0 + e];
+                a0 = fmaf(wk, v[e], a0);
+                a1 = fmaf(wk, v[e + 1], a1);
+                a2 = fmaf(wk, v[e + 2], a2);
+                a3 = fmaf(wk, v[e + 3], a3);
+            }
+        }
+        lo = hi;
+    }
+    float *o = p.out + (size_t)j * p.nx + ib;
+    o[0] = a0;
+    if (ib + 1 < p.nx) o[1] = a1;
+    if (ib + 2 < p.nx) o[2] = a2;
+    if (ib + 3 < p.nx) o[3] = a3;
 }
 
-// out[j][i] = sum_k w[k] in[clamp(j + k - r)][i]; a CTA of 32 x 8 threads
-// covers 32 columns and kColTile rows.
+// out[j][i] = sum_k w[k] in[clamp(j + k - r)][i], each sum over k in order; a
+// CTA of 32 x 8 threads covers 32 columns and kColTile rows, thread (x, y)
+// rows 8y .. 8y+7 of column x from a window of sixteen tile rows refilled
+// with eight loads per eight taps.
 __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
 {
     extern __shared__ float sm[];
     float *w = sm;                           // 2r + 1, padded to a multiple of 32
-    float *tile = sm + ((2 * p.r + 1 + 31) & ~31);   // [kColTile + 2r][32]
+    float *tile = sm + ((2 * p.r + 1 + 31) & ~31);   // [kColTile + 2r + 8][32]
     gauss_weights(w, p.r, p.inv2s2);
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j0 = blockIdx.y * kColTile;
     const int ic = min(i, p.nx - 1);
-    for (int t = threadIdx.y; t < kColTile + 2 * p.r; t += 8)
+    const int n_rows = kColTile + 2 * p.r + 8;
+    for (int t = threadIdx.y; t < n_rows; t += 8)
         tile[t * 32 + threadIdx.x] = __ldg(p.in + (size_t)clampi(j0 - p.r + t, 0, p.ny - 1) * p.nx + ic);
     __syncthreads();
-    if (i >= p.nx) return;
-    for (int jj = threadIdx.y; jj < kColTile; jj += 8) {
-        const int j = j0 + jj;
-        if (j >= p.ny) break;
-        float acc = 0.f;
-        for (int k = 0; k <= 2 * p.r; ++k) acc = fmaf(w[k], tile[(jj + k) * 32 + threadIdx.x], acc);
-        p.out[(size_t)j * p.nx + i] = acc;
+    const int jb = kColOut * threadIdx.y;    // first of this thread's rows in the tile
+    if (i >= p.nx || j0 + jb >= p.ny) return;
+    const float *col = tile + jb * 32 + threadIdx.x;
+    float acc[kColOut];
+    float v[2 * kColOut];
+#pragma unroll
+    for (int q = 0; q < kColOut; ++q) {
+        acc[q] = 0.f;
+        v[q] = col[q * 32];
+    }
+    const int n = 2 * p.r + 1;
+    for (int k0 = 0; k0 < n; k0 += kColOut) {
+#pragma unroll
+        for (int q = 0; q < kColOut; ++q) v[kColOut + q] = col[(k0 + kColOut + q) * 32];
+#pragma unroll
+        for (int e = 0; e < kColOut; ++e) {
+            if (k0 + e < n) {
+                const float wk = w[k0 + e];
+#pragma unroll
+                for (int q = 0; q < kColOut; ++q) acc[q] = fmaf(wk, v[e + q], acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kColOut; ++q) v[q] = v[kColOut + q];
+    }
+#pragma unroll
+    for (int q = 0; q < kColOut; ++q) {
+        const int j = j0 + jb + q;
+        if (j < p.ny) p.out[(size_t)j * p.nx + i] = acc[q];
     }
 }
 
-size_t rows_smem(int r) { return sizeof(float) * (size_t)(2 * r + 1 + kRowTile + 2 * r); }
+size_t rows_smem(int r) { return sizeof(float) * (size_t)(((2 * r + 1 + 3) & ~3) + kRowTile + 2 * r + 8); }
 size_t cols_smem(int r)
 {
-    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (kColTile + 2 * r) * 32);
+    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (kColTile + 2 * r + 8) * 32);
 }
 
 }  // namespace
@@ -130,7 +182,7 @@ cudaError_t launch_lod_smooth(const float *in, float *tmp, float *out, int nx, i
     p.inv2s2 = inv2s2;
     p.in = in;
     p.out = tmp;
-    lod_rows_kernel<<<dim3((unsigned)((nx + kRowTile - 1) / kRowTile), (unsigned)ny), kRowTile,
+    lod_rows_kernel<<<dim3((unsigned)((nx + kRowTile - 1) / kRowTile), (unsigned)ny), kRowThreads,
                       rows_smem(r), stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
