@@ -201,6 +201,8 @@ cudaError_t launch_lod_smooth(const float *in, float *tmp, float *out, int nx, i
 namespace {
 
 constexpr int kChunk = 256;       // vertices staged per pass, one per thread
+// the tile's perimeter scan takes one thread of the 16 x 16 CTA per perimeter
+static_assert(kCostmapMaxPolys <= 256, "one costmap thread per perimeter");
 
 // Bounding box of perimeter blockIdx.x in the costmap kernel's coordinates,
 // grown by `reach`; one warp per perimeter.
