@@ -102,7 +102,8 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms, each sample
+    stamped on arrival so that only those taken inside the timed region count."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -115,18 +116,24 @@ class ClockSampler:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-i", str(self.index), "-lms", "200"],
+                                       "-i", str(self.index), "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
             self.p = None
+            return
+        t0 = time.perf_counter()             # wait for the sampler to run
+        while not self.lines and time.perf_counter() - t0 < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.p.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, t_begin, t_end):
+        """Summary of the samples stamped in [t_begin, t_end] (perf_counter
+        seconds); the nearest sample when none falls inside."""
         if self.p is None:
             return None
         self.p.terminate()
@@ -136,7 +143,10 @@ class ClockSampler:
             self.p.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        inside = [l for t, l in self.lines if t_begin <= t <= t_end]
+        if not inside and self.lines:
+            inside = [min(self.lines, key=lambda tl: abs(tl[0] - 0.5 * (t_begin + t_end)))[1]]
+        for l in inside:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -151,7 +161,7 @@ class ClockSampler:
         if not sm:
             return None
         return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm),
-                    reasons=sorted(reasons))
+                    reasons=sorted(reasons), window="samples stamped inside the timed region")
 
 
 def make_workload(name):
@@ -382,7 +392,7 @@ def run_serving(seconds, device):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scaled", choices=["scaled", "plain", "paper"])
@@ -432,12 +442,12 @@ def main():
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
+    t_begin = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()                       # evict L2 between steps
         ev[i][0].record(stream)
@@ -446,9 +456,10 @@ def main():
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
+    t_end = time.perf_counter()
     per_step = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(per_step)
-    clk = clocks.stop()
+    clk = clocks.stop(t_begin, t_end)
     ms = max_over_ranks(ms, dev)
     units = w.N * w.H
     value = job_rate(ws, units, ms)
