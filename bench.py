@@ -287,6 +287,8 @@ def run_paper_config(ctx, dev, stream, flush, steps=10, warmup=3):
                         f"each), steering only, {w.terrain.nx}^2 heightmap at {w.terrain.cell} m",
             "ms_per_plan": ms, "planner_hz": 1000.0 / ms, "samples_per_s": w.N / (ms / 1000),
             "substeps_per_s": w.N * w.H * w.n_sub / (ms / 1000),
+            "fp32_tflops": FLOPS_PER_SUBSTEP * w.N * w.H * w.n_sub / (ms / 1000) / 1e12,
+            "fp32_frac": FLOPS_PER_SUBSTEP * w.N * w.H * w.n_sub / (ms / 1000) / 1e12 / fp32_peak_tflops(),
             "paper_context": "80 Hz, over 11 M samples/s on an RTX 5000 Ada Mobile; about 21 M "
                              "samples/s on an RTX 6000 Ada (Sec. IV-D); other hardware"}
 
