@@ -97,6 +97,16 @@ TERRAIN = [
  ("crossing half-open", "if ((ay > py) != (by > py)) {", "if ((ay >= py) != (by > py)) {"),
 ]
 
+SAMPLER = [
+ ("rounds 9", "for (r = 0; r < 10; ++r) {", "for (r = 0; r < 9; ++r) {"),
+ ("key bumped before the first round", "if (r > 0) {", "if (r >= 0) {"),
+ ("word order", "n[1] = lo1;", "n[1] = lo0;"),
+ ("shift ignored", "int src = k + shift;", "int src = k;"),
+ ("sin for both", "sigma_rate * r * cos(2.0 * M_PI * u2)", "sigma_rate * r * sin(2.0 * M_PI * u2)"),
+ ("sigmas swapped", "o[0] = nom[0] + sigma_rate", "o[0] = nom[0] + sigma_acc"),
+ ("nominal at candidate 1", "if (j == 0) {", "if (j == 1) {"),
+]
+
 EQUIVALENT = {("srb.c", "Fx on front"), ("terrain_tools.c", "ray direction")}
 
 
@@ -129,6 +139,7 @@ def run(fname, mutations, test):
 
 if __name__ == "__main__":
     missed = (run("srb.c", SRB, "test_oracle_pins.py") + run("est.c", EST, "test_oracle_est.py") +
-              run("terrain_tools.c", TERRAIN, "test_oracle_terrain_tools.py"))
+              run("terrain_tools.c", TERRAIN, "test_oracle_terrain_tools.py") +
+              run("sampler.c", SAMPLER, "test_oracle_sampler.py"))
     print("missed:", missed or "none beyond the two equivalent changes")
     sys.exit(1 if missed else 0)
