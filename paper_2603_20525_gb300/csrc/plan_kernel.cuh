@@ -35,7 +35,7 @@ struct PlanParams {
     float *step_margin;       // [H][N] or nullptr
     int tex_format;           // TEX_F32 or TEX_BF16
     int acc64;                // accumulate the running cost in FP64
-    int lanes;                // 0: by batch size; 1 or 4 lanes per candidate
+    int lanes;                // 0: by batch size; else 1, 2 or 4 lanes per candidate
     // plan only
     atp_plan_out *out;
     float *best_ctrl;         // [H][2] or nullptr
