@@ -107,6 +107,19 @@ SAMPLER = [
  ("nominal at candidate 1", "if (j == 0) {", "if (j == 1) {"),
 ]
 
+ADJOINT = [
+ ("d sin sign", "inline AD sin(const AD &a) { return mk(std::sin(a.v), a, std::cos(a.v)); }",
+  "inline AD sin(const AD &a) { return mk(std::sin(a.v), a, -std::cos(a.v)); }"),
+ ("d cos sign", "inline AD cos(const AD &a) { return mk(std::cos(a.v), a, -std::sin(a.v)); }",
+  "inline AD cos(const AD &a) { return mk(std::cos(a.v), a, std::sin(a.v)); }"),
+ ("d sqrt factor", "return mk(r, a, r > 0 ? 0.5 / r : 0.0); }", "return mk(r, a, r > 0 ? 1.0 / r : 0.0); }"),
+ ("d quotient sign", "b, -a.v / (b.v * b.v)); }", "b, a.v / (b.v * b.v)); }"),
+ ("d product swapped", "return mk2(a.v * b.v, a, b.v, b, a.v); }", "return mk2(a.v * b.v, a, a.v, b, b.v); }"),
+ ("d atan2 swapped", "return mk2(std::atan2(y.v, x.v), y, x.v / r2, x, -y.v / r2);",
+  "return mk2(std::atan2(y.v, x.v), y, -y.v / r2, x, x.v / r2);"),
+ ("d fabs", "return mk(std::fabs(a.v), a, a.v < 0 ? -1.0 : 1.0); }", "return mk(std::fabs(a.v), a, 1.0); }"),
+]
+
 EQUIVALENT = {("srb.c", "Fx on front"), ("terrain_tools.c", "ray direction")}
 
 
@@ -140,6 +153,7 @@ def run(fname, mutations, test):
 if __name__ == "__main__":
     missed = (run("srb.c", SRB, "test_oracle_pins.py") + run("est.c", EST, "test_oracle_est.py") +
               run("terrain_tools.c", TERRAIN, "test_oracle_terrain_tools.py") +
-              run("sampler.c", SAMPLER, "test_oracle_sampler.py"))
+              run("sampler.c", SAMPLER, "test_oracle_sampler.py") +
+              run("adjoint.cpp", ADJOINT, "test_oracle_adjoint.py"))
     print("missed:", missed or "none beyond the two equivalent changes")
     sys.exit(1 if missed else 0)

@@ -108,3 +108,43 @@ def test_autograd_function_and_refinement(setup):
     print("refinement: mean cost", h[0].mean(), "->", h[-1].mean(), "improved", np.mean(h[-1] < h[0]))
     assert np.mean(h[-1] < h[0]) > 0.8
     assert float(ctrl[..., 0].abs().max()) <= w.vehicle["delta_rate_max"]
+
+
+@pytest.mark.parametrize("slope_deg", [37.0, -37.0])
+def test_gradient_with_the_esm_soft_term_active(slope_deg):
+    """A 37-degree cross slope rolls the chassis to |phi| ~ 0.65 rad, where
+    the ESM is under 10 % of its level-ground value and its soft cost is
+    active on every step: the GPU adjoint through |phi| and the soft term
+    against the FP64 tape adjoint."""
+    import math
+    from paper_2603_20525_gb300 import atp
+    ctx = atp.Context(0)
+    try:
+        v = gen.vehicle_baseline()
+        c = gen.cost_default(1000.0, 0.0)
+        n, cell = 256, 0.5
+        ys = np.arange(n) * cell - 64.0
+        hts = np.repeat((math.tan(math.radians(slope_deg)) * ys)[:, None], n, axis=1).astype(np.float32)
+        ter_g = gen.Terrain(hts, cell, -10.0, -64.0)
+        x0 = gen.settled_state(ter_g, v, 0.0, 0.0, 0.0, 6.0)
+        H, dt, n_sub, K = 20, 0.05, 5, 16
+        rng = np.random.default_rng(1)
+        ctrl = np.stack([rng.normal(0, 0.2, (H, K)), rng.normal(0, 0.3, (H, K))], -1).astype(np.float32)
+        ter = ctx.terrain_prepare(torch.as_tensor(hts).cuda(), cell, -10.0, -64.0)
+        J, G = ctx.grad(v, c, ter, [float(q) for q in x0], torch.as_tensor(ctrl).cuda(), dt, n_sub)
+        torch.cuda.synchronize()
+        Jg, Gg = J.cpu().numpy().astype(np.float64), G.cpu().numpy().astype(np.float64)
+        t = oracle.Terrain(hts, cell, -10.0, -64.0)
+        Jo, Go = oracle.grad(v, c, t, x0, ctrl, dt, n_sub)
+        assert Jo.min() > 1e5                        # the soft term dominates the cost
+        assert np.max(np.abs(Jg - Jo) / Jo) < 1e-4
+        num = np.linalg.norm((Gg - Go).reshape(-1, K), axis=0)
+        den = np.linalg.norm(Go.reshape(-1, K), axis=0)
+        rel = num / den
+        cos = np.sum((Gg * Go).reshape(-1, K), 0) / (np.linalg.norm(Gg.reshape(-1, K), axis=0) * den)
+        print("side slope", slope_deg, "gradient relative error: median", np.median(rel), "max", rel.max(),
+              "cosine min", cos.min())
+        assert np.median(rel) < 1e-4 and rel.max() < 1e-3
+        assert cos.min() > 0.99999
+    finally:
+        ctx.close()

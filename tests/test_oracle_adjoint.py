@@ -79,3 +79,41 @@ def test_gradient_against_central_differences():
                 smooth += 1
                 assert G[k, j, c] == pytest.approx(a, rel=2e-4, abs=2e-4), (j, k, c)
     assert smooth >= 0.7 * checked
+
+
+@pytest.mark.parametrize("slope_deg", [37.0, -37.0])
+def test_gradient_with_the_esm_soft_term_active(slope_deg):
+    """A 37-degree cross slope rolls the chassis to |phi| ~ 0.65 rad, to one
+    side or the other, where the ESM is under 10 % of its level-ground value
+    and its soft cost (Sec. IV-B, IV-C) is active: the gradient through
+    |phi| and the soft term against FP64 central differences."""
+    import math
+    v = gen.vehicle_baseline()
+    c = gen.cost_default(1000.0, 0.0)
+    n, cell = 256, 0.5
+    ys = np.arange(n) * cell - 64.0
+    hts = np.repeat((math.tan(math.radians(slope_deg)) * ys)[:, None], n, axis=1).astype(np.float32)
+    ter = gen.Terrain(hts, cell, -10.0, -64.0)
+    t = oracle.Terrain(hts, cell, -10.0, -64.0)
+    x0 = gen.settled_state(ter, v, 0.0, 0.0, 0.0, 6.0)
+    H, dt, n_sub = 20, 0.05, 5
+    rng = np.random.default_rng(1)
+    ctrl = np.stack([rng.normal(0, 0.2, (H, 4)), rng.normal(0, 0.3, (H, 4))], -1).astype(np.float32)
+    w = gen.Workload("side-slope", ter, v, c, x0, ctrl, dt, n_sub)
+    tr = oracle.trajectory(v, c, t, x0, ctrl[:, 0, :], dt, n_sub)
+    states = tr["states"] if isinstance(tr, dict) else tr[0]
+    assert np.all(np.sign(states[:, 5]) == math.copysign(1.0, slope_deg))   # rising to the left: positive roll
+    u_min = min(oracle.esm(v, float(p), float(q)) for p, q in zip(states[:, 5], states[:, 4]))
+    assert u_min < 0.1 * oracle.esm(v, 0.0, 0.0)
+    J, G = oracle.grad(v, c, t, x0, ctrl, dt, n_sub)
+    smooth = checked = 0
+    for j in range(4):
+        for k in (0, 3, 7, 12, 18):
+            for comp in (0, 1):
+                a, b = fd(w, t, j, k, comp, 1e-6), fd(w, t, j, k, comp, 1e-5)
+                checked += 1
+                if abs(a - b) > 1e-3 * max(abs(a), 1e-2):
+                    continue
+                smooth += 1
+                assert G[k, j, comp] == pytest.approx(a, rel=2e-4, abs=2e-4), (j, k, comp)
+    assert smooth >= 0.7 * checked
