@@ -228,6 +228,37 @@ def test_ragged_sizes(ctx, N, H, n_sub):
     check_plan(gpu_plan(ctx, w), oracle_plan(w), w)
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("slope_deg", [37.0, -37.0])
+def test_steep_cross_slope_with_the_soft_constraint_active(ctx, slope_deg, lanes):
+    """A 37-degree cross slope, rising to either side, rolls the chassis to
+    |phi| ~ 0.65 rad while it slides down the slope: the ESM is under 10 % of
+    its level-ground value, so its soft cost (Sec. IV-B, IV-C) is active at
+    every step, for either sign of the roll, in every thread layout."""
+    from paper_2603_20525_gb300 import atp
+    v = gen.vehicle_baseline()
+    c = gen.cost_default(1000.0, 0.0)
+    n, cell = 256, 0.5
+    ys = np.arange(n) * cell - 64.0
+    hts = np.repeat((math.tan(math.radians(slope_deg)) * ys)[:, None], n, axis=1).astype(np.float32)
+    ter = gen.Terrain(hts, cell, -10.0, -64.0)
+    x0 = gen.settled_state(ter, v, 0.0, 0.0, 0.0, 6.0)
+    H, dt, N = 20, 0.05, 1500
+    rng = np.random.default_rng(2)
+    ctrl = np.stack([rng.normal(0, 0.2, (H, N)), rng.normal(0, 0.3, (H, N))], -1).astype(np.float32)
+    w = gen.Workload("cross-slope", ter, v, c, x0, ctrl, dt, gen.n_substeps(dt))
+    ctx.set_option(atp.OPT_LANES, lanes)
+    try:
+        g = gpu_plan(ctx, w)
+    finally:
+        ctx.set_option(atp.OPT_LANES, 0)
+    o = oracle_plan(w)
+    U0 = parity.level_esm(v)
+    assert np.all(o["margin"] < 0.1 * U0)           # the soft term acts on every candidate
+    assert np.all(o["J"] > 1e5)
+    check_plan(g, o, w)
+
+
 def test_all_infeasible_and_ties(ctx):
     w = gen.workload_plain(5, N=96, H=10)
     x0 = np.repeat(w.x0[None, :], w.N, axis=0)
