@@ -82,15 +82,29 @@ def test_bf16_plan_parity_with_decoded_terrain(ctx, seed):
     assert g["best_idx"] == int(np.lexsort((np.arange(w.N), g["cost"], (g["flags"] & 1) == 0))[0])
 
 
-def test_fp64_cost_accumulation_changes_cost_only(ctx):
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_fp64_cost_accumulation_changes_cost_only(ctx, lanes):
+    """In every thread layout (each has its own FP64-accumulating kernel),
+    and through the batch kernel, which takes the choice at run time."""
     from paper_2603_20525_gb300 import atp
     w = gen.workload_plain(1)
     ter = ctx.terrain_prepare(dev(w.terrain.heights), w.terrain.cell)
     args = (w.vehicle, w.cost, ter, [float(v) for v in w.x0], dev(w.ctrl), w.dt, w.n_sub)
-    a = ctx.plan(*args, want_xf=True)
-    ctx.set_option(atp.OPT_COST_FP64, 1)
-    b = ctx.plan(*args, want_xf=True)
-    ctx.set_option(atp.OPT_COST_FP64, 0)
+    ctx.set_option(atp.OPT_LANES, lanes)
+    try:
+        a = ctx.plan(*args, want_xf=True)
+        ctx.set_option(atp.OPT_COST_FP64, 1)
+        b = ctx.plan(*args, want_xf=True)
+        # the batch kernel, with the same forced layout, takes FP64 at run time
+        q = dict(veh=w.vehicle, cost=w.cost, terrain=ter, x0=[float(v) for v in w.x0],
+                 ctrl=dev(w.ctrl), dt=w.dt, n_sub=w.n_sub, out=atp.plan_outputs(w.N, w.H, xf=True))
+        ctx.plan_batch([q])
+        torch.cuda.synchronize()
+        for k in ("cost", "margin", "flags", "xf"):
+            assert torch.equal(q["out"][k], b[k]), k
+    finally:
+        ctx.set_option(atp.OPT_COST_FP64, 0)
+        ctx.set_option(atp.OPT_LANES, 0)
     torch.cuda.synchronize()
     for k in ("margin", "flags", "xf"):
         assert torch.equal(a[k], b[k]), k
