@@ -8,8 +8,13 @@
 //     sub-partition several warps.  The state stays in registers for the
 //     whole horizon; per Euler step the only memory traffic is 16 terrain
 //     texels (four bilinear lookups of one float4 per corner) through the
-//     read-only path, which the L1 and the 126 MB L2 serve for every terrain
+//     read-only path, which the L1 and the 129 MB L2 serve for every terrain
 //     size used.
+//   * The arithmetic forms that measured faster in only some layouts are
+//     compile-time choices that give the same bits: the running cost's
+//     accumulator (FP32 or FP64), packed two-wide FP32 pairs and a goal
+//     test that discards the step rather than branching (two lanes), and
+//     loading each control one interval ahead (four lanes).
 //   * Controls are time-major float2 [H][N]: a warp reads one coalesced 256 B
 //     line per control step.
 //   * The reduction is fused into the tail: a warp-shuffle min of a packed
