@@ -8,7 +8,8 @@
 // texels).
 //
 // Precision.  The arithmetic is FP32, compiled without implicit FMA
-// contraction: every fused multiply-add is written as fmaf, so the rounding
+// contraction: every fused multiply-add is written as fmaf (or as fma2, its
+// packed two-wide form, which rounds each half the same way), so the rounding
 // of each expression is fixed by the source and the same in every kernel that
 // inlines it.  The slowly varying, large-magnitude
 // state components (position, heading and linear velocity) are accumulated as
