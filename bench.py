@@ -390,14 +390,18 @@ def run_serving(seconds, device):
     serve.reset_warm_start(vehicles)
     trace = serve.poisson_trace(32, 20.0, seconds, seed=1)
     served = srv.serve(trace)
+    gap_served = srv.max_loop_gap
     serve.reset_warm_start(vehicles)
     plain = srv.sequential(trace)
+    gap_plain = srv.max_loop_gap
     same = all(a.best_idx == b.best_idx and a.best_cost == b.best_cost for a, b in zip(served, plain))
     return {"workload": "32 vehicles x 20 Hz Poisson, N in {1024, 4096, 16384, 32768}, "
                         "H 40-150, dt 0.02-0.05 s, own 512-2048^2 tile at 0.1 m, warm start",
             "trace_s": seconds, "requests": len(trace),
-            "served": serve.latency_summary(served),
-            "plain_sequential": serve.latency_summary(plain),
+            "served": dict(serve.latency_summary(served),
+                           longest_loop_pause_ms=1000 * gap_served[0], at_s=gap_served[1]),
+            "plain_sequential": dict(serve.latency_summary(plain),
+                                     longest_request_ms=1000 * gap_plain[0], at_s=gap_plain[1]),
             "identical_results": bool(same)}
 
 

@@ -222,6 +222,10 @@ class Server:
         self.inflight = [None] * streams
         self.pinned = torch.empty((self.max_batch * streams, 6), dtype=torch.int32).pin_memory()
         self.h_max = h_max
+        # (seconds, trace time): the longest interval between two passes of
+        # the serving loop (served) or the longest launch-to-result time
+        # (sequential) in the last run; a host stall shows up here
+        self.max_loop_gap = (0.0, 0.0)
 
     # -- per request -----------------------------------------------------
     def _buffers(self, off, N, H):
@@ -264,8 +268,12 @@ class Server:
         pi = 0
         done = 0
         t0 = time.perf_counter()
+        t_prev, self.max_loop_gap = 0.0, (0.0, 0.0)
         while done < len(trace):
             now = time.perf_counter() - t0
+            if now - t_prev > self.max_loop_gap[0]:      # the host loop's longest pause
+                self.max_loop_gap = (now - t_prev, t_prev)
+            t_prev = now
             while pi < len(pending) and pending[pi].t_arrive <= now:
                 queue.append(pending[pi])
                 pi += 1
@@ -325,6 +333,7 @@ class Server:
         out_host = self.pinned[0:1]
         recs = []
         t0 = time.perf_counter()
+        self.max_loop_gap = (0.0, 0.0)
         for r in trace:
             while time.perf_counter() - t0 < r.t_arrive:
                 time.sleep(2e-5)
@@ -346,6 +355,8 @@ class Server:
                 out_host[0].copy_(b["out"], non_blocking=True)
             stream.synchronize()
             rec.t_done = time.perf_counter() - t0
+            if rec.t_done - rec.t_launch > self.max_loop_gap[0]:
+                self.max_loop_gap = (rec.t_done - rec.t_launch, rec.t_launch)
             rec.best_idx = int(out_host[0, 0])
             rec.best_cost = float(out_host[0, 2:3].view(torch.float32)[0])
             rec.batch = 1
