@@ -23,7 +23,7 @@ import contextlib
 import gc
 import math
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
