@@ -428,9 +428,9 @@ def main():
     from paper_2603_20525_gb300 import atp
 
     ws, rank, local = dist_env()
+    torch.cuda.set_device(local)            # each rank's own GPU before NCCL comes up
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
