@@ -120,6 +120,16 @@ ADJOINT = [
  ("d fabs", "return mk(std::fabs(a.v), a, a.v < 0 ? -1.0 : 1.0); }", "return mk(std::fabs(a.v), a, 1.0); }"),
 ]
 
+BF16 = [
+ ("round half up", "b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16", "b = (b + 0x8000) >> 16"),
+ ("truncate", "b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16", "b = b >> 16"),
+ ("slope over n", "f32(f32(1.0) / f32(ni - 1))) if ni > 1", "f32(f32(1.0) / f32(ni))) if ni > 1"),
+ ("plane through the block centre", "c0 = H[j0, i0]", "c0 = H[j0 + nj // 2, i0 + ni // 2]"),
+ ("plane slopes not removed", "w_gx = bf16_round((g.gx.astype(np.float32) - px).astype(np.float32))",
+  "w_gx = bf16_round(g.gx.astype(np.float32))"),
+ ("y slope from x", "py = (P[..., 2] * inv).astype(np.float32)", "py = (P[..., 1] * inv).astype(np.float32)"),
+]
+
 EQUIVALENT = {("srb.c", "Fx on front"), ("terrain_tools.c", "ray direction")}
 
 
@@ -154,6 +164,7 @@ if __name__ == "__main__":
     missed = (run("srb.c", SRB, "test_oracle_pins.py") + run("est.c", EST, "test_oracle_est.py") +
               run("terrain_tools.c", TERRAIN, "test_oracle_terrain_tools.py") +
               run("sampler.c", SAMPLER, "test_oracle_sampler.py") +
-              run("adjoint.cpp", ADJOINT, "test_oracle_adjoint.py"))
+              run("adjoint.cpp", ADJOINT, "test_oracle_adjoint.py") +
+              run("__init__.py", BF16, "test_oracle_bf16.py"))
     print("missed:", missed or "none beyond the two equivalent changes")
     sys.exit(1 if missed else 0)
