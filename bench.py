@@ -185,6 +185,18 @@ def workload_config(w, name):
             "l2": "flushed between steps (256 MB write)"}
 
 
+def omp_threads() -> int:
+    """Threads the oracle's OpenMP loops run with: OMP_NUM_THREADS if set,
+    else one per CPU this process may run on (libgomp's default)."""
+    env = os.environ.get("OMP_NUM_THREADS", "").split(",")[0].strip()
+    if env.isdigit() and int(env) > 0:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def run_reference(args, w, name, budget_s=120.0):
     """The FP64 CPU oracle, as it stands, on the same workload.  Each step
     plans a prefix of the candidates, sized from one timed full plan so that
@@ -194,7 +206,7 @@ def run_reference(args, w, name, budget_s=120.0):
     if rank != 0:
         return
     t = oracle.Terrain.of(w.terrain)
-    cores = os.cpu_count() or 1
+    cores = omp_threads()
     t0 = time.perf_counter()
     oracle.plan(w.vehicle, w.cost, t, w.x0, w.ctrl, w.dt, w.n_sub)
     t_full = time.perf_counter() - t0
@@ -238,7 +250,7 @@ def cpu_baseline(w, budget_s=10.0):
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 200:
             break
-    out = {"value": n * w.N * w.H / el, "unit": "rollout-steps/s", "cores": os.cpu_count() or 1,
+    out = {"value": n * w.N * w.H / el, "unit": "rollout-steps/s", "cores": omp_threads(),
            "kind": "oracle",
            "sample": f"{n} whole plans of the workload ({n * w.N} candidates, {el:.1f} s), FP64"}
     # the same oracle on one thread, over the first 1024 candidates

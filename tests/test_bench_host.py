@@ -71,3 +71,10 @@ def test_clock_window_falls_back_to_the_nearest_sample():
 def test_clock_sampler_without_nvidia_smi_reports_nothing():
     c = bench.ClockSampler(0)
     assert c.stop(0.0, 1.0) is None
+
+
+def test_omp_threads_follows_the_environment(monkeypatch):
+    monkeypatch.setenv("OMP_NUM_THREADS", "3")
+    assert bench.omp_threads() == 3
+    monkeypatch.delenv("OMP_NUM_THREADS")
+    assert bench.omp_threads() == len(os.sched_getaffinity(0))
