@@ -33,18 +33,35 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic FP32 work of one Euler step of one candidate, counted from the
-# model's equations (FMA = 2 flops): rotation 20, ESM 6, goal test 5, gravity 3,
-# four wheels 4 x 107, force and moment sums 30, running cost 14, state
-# derivative 49, Euler update 26.  The 20 special functions per step (3 sincos,
-# cos(delta), 4 atan2, 4 rsqrt, 5 reciprocals) are not in the flop count.
-FLOPS_PER_SUBSTEP = 581
-SPECIAL_PER_SUBSTEP = 20
-SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+# Algorithmic FP32 work of one Euler step of one candidate: the additions,
+# subtractions, multiplications and divisions of the oracle's model, counted by
+# its counting scalar (oracle.count_ops) over the first 1024 candidates of each
+# workload; tests/test_bench_host.py recounts them.  A fused multiply-add is
+# two of these.  The elementary functions of a step (5 sqrt, 4 sin, 8 cos and
+# 4 atan2 in the oracle's form) are not in the count.
+FLOPS_PER_SUBSTEP = {"plain": 623.762, "scaled": 623.070, "paper": 622.553}
+FP32_LANES_PER_SM = 128         # FP32 units per Blackwell SM (4 sub-partitions x 32)
 
 
-def fp32_peak_tflops(mhz=MAX_SM_MHZ):
-    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+def device_sm_count(device=0) -> int:
+    """Streaming multiprocessors of the GPU, from the device properties."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def max_sm_mhz(index=0):
+    """The GPU's maximum SM clock (nvidia-smi clocks.max.sm), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", str(index)], capture_output=True, text=True, timeout=30).stdout
+        return float(out.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return None
+
+
+def fp32_peak_tflops(sms, mhz):
+    """SMs x 128 FP32 lanes x 2 flops (fused multiply-add) x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
 def kernel_sources_sha256():
@@ -269,7 +286,7 @@ def cpu_baseline(w, budget_s=10.0):
     return out
 
 
-def run_paper_config(ctx, dev, stream, flush, steps=10, warmup=3):
+def run_paper_config(ctx, dev, stream, flush, peak, steps=10, warmup=3):
     """The real-time configuration of Sec. IV-D (204,288 candidates, 16 steps
     of 0.25 s, 800 Euler steps of 5 ms each, steering only) on this GPU, in
     the paper's units: trajectory samples per second and the planner rate.
@@ -298,8 +315,8 @@ def run_paper_config(ctx, dev, stream, flush, steps=10, warmup=3):
                         f"each), steering only, {w.terrain.nx}^2 heightmap at {w.terrain.cell} m",
             "ms_per_plan": ms, "planner_hz": 1000.0 / ms, "samples_per_s": w.N / (ms / 1000),
             "substeps_per_s": w.N * w.H * w.n_sub / (ms / 1000),
-            "fp32_tflops": FLOPS_PER_SUBSTEP * w.N * w.H * w.n_sub / (ms / 1000) / 1e12,
-            "fp32_frac": FLOPS_PER_SUBSTEP * w.N * w.H * w.n_sub / (ms / 1000) / 1e12 / fp32_peak_tflops(),
+            "fp32_tflops": FLOPS_PER_SUBSTEP["paper"] * w.N * w.H * w.n_sub / (ms / 1000) / 1e12,
+            "fp32_frac": FLOPS_PER_SUBSTEP["paper"] * w.N * w.H * w.n_sub / (ms / 1000) / 1e12 / peak,
             "paper_context": "80 Hz, over 11 M samples/s on an RTX 5000 Ada Mobile; about 21 M "
                              "samples/s on an RTX 6000 Ada (Sec. IV-D); other hardware"}
 
@@ -547,8 +564,11 @@ def main():
 
     if rank == 0:
         substeps = units * w.n_sub
-        achieved = FLOPS_PER_SUBSTEP * substeps / (ms / 1000) / 1e12
-        peak = fp32_peak_tflops()
+        flops = FLOPS_PER_SUBSTEP[args.workload]
+        achieved = flops * substeps / (ms / 1000) / 1e12
+        sms = device_sm_count(local)
+        mhz = max_sm_mhz(local) or (clk or {}).get("sm_max_mhz") or 2070.0
+        peak = fp32_peak_tflops(sms, mhz)
         line = {
             "metric": "rollout-steps/s", "value": value, "unit": "rollout-steps/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -561,9 +581,10 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
                          "kernel": "plan_kernel (fused rollout + argmin)",
-                         "note": f"{FLOPS_PER_SUBSTEP} algorithmic FP32 flops per Euler step x "
-                                 f"{substeps} Euler steps per launch; peak = 152 SMs x 128 FP32 "
-                                 f"lanes x 2 x 2070 MHz (derived)"},
+                         "note": f"{flops} algorithmic FP32 flops per Euler step (counted by the "
+                                 f"oracle's counting scalar) x {substeps} Euler steps per launch; "
+                                 f"peak = {sms} SMs (device query) x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                 f"x {mhz:g} MHz (maximum SM clock, nvidia-smi), derived"},
             "e2e": {"value": job_rate(ws, units, e2e_ms), "unit": "rollout-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                     "overlap": "step k+1's inputs are copied on a second stream while step k runs "
@@ -572,7 +593,7 @@ def main():
             "clocks": clk,
         }
         if args.workload != "paper":
-            line["paper_configuration"] = run_paper_config(ctx, dev, stream, flush)
+            line["paper_configuration"] = run_paper_config(ctx, dev, stream, flush, peak)
             line["other_kernels"] = run_variants(ctx, dev, stream, flush)
         if args.serve_seconds > 0:
             line["serving"] = run_serving(args.serve_seconds, local)

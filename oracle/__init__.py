@@ -18,8 +18,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = [os.path.join(_HERE, n) for n in ("srb.c", "sampler.c", "est.c", "terrain_tools.c")]
-_SRC_CXX = [os.path.join(_HERE, "adjoint.cpp")]
-_HDR = [os.path.join(_HERE, "oracle.h")]
+_SRC_CXX = [os.path.join(_HERE, n) for n in ("adjoint.cpp", "emul32.cpp")]
+_HDR = [os.path.join(_HERE, n) for n in ("oracle.h", "model.hpp")]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -138,6 +138,16 @@ def lib():
             L.orc_lod_smooth.argtypes = [_fp, C.c_int, C.c_int, C.c_double, C.c_double, _dp]
             L.orc_lod_smooth.restype = C.c_int
             _ip = C.POINTER(C.c_int)
+            _roll = [C.c_int, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain), _fp, C.c_int,
+                     _fp, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp, _up, _dp, _ip]
+            L.orc_rollout_f32.argtypes = _roll
+            L.orc_rollout_f32.restype = C.c_int
+            L.orc_rollout_templated.argtypes = _roll
+            L.orc_rollout_templated.restype = C.c_int
+            L.orc_count_ops.argtypes = [C.c_int, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
+                                        _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                        C.POINTER(C.c_long)]
+            L.orc_count_ops.restype = C.c_int
             L.orc_sdist.argtypes = [_dp, C.c_int, C.c_int, C.c_double, C.c_double]
             L.orc_sdist.restype = C.c_double
             L.orc_costmap.argtypes = [_dp, _ip, _ip, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -377,6 +387,58 @@ def cost_f64(veh: dict, cst: dict, ter: Terrain, x0, u, dt: float, n_sub: int):
     u = np.ascontiguousarray(u, dtype=np.float64)
     return lib().orc_cost_f64(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
                               _ptr(x0, _dp), _ptr(u, _dp), u.shape[0], float(dt), int(n_sub))
+
+
+# ---- The templated model (model.hpp): FP32 reference, restatement check, operation count
+def _templated(fn, model, veh, cst, ter, x0, ctrl, dt, n_sub):
+    n = 13 if model == "srb" else 7
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
+    H, N, _ = ctrl.shape
+    per = 1 if x0.ndim == 2 else 0
+    J = np.empty(N)
+    margin = np.empty(N)
+    flags = np.empty(N, dtype=np.uint8)
+    xf = np.empty((N, n))
+    ms = np.empty(N, dtype=np.int32)
+    rc = fn(0 if model == "srb" else 1, C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+            _ptr(x0, _fp), per, _ptr(ctrl, _fp), N, H, float(dt), int(n_sub), _ptr(J, _dp),
+            _ptr(margin, _dp), _ptr(flags, _up), _ptr(xf, _dp), _ptr(ms, C.POINTER(C.c_int)))
+    if rc != 0:
+        raise ValueError("templated rollout rejected its arguments")
+    return dict(J=J, margin=margin, flags=flags, xf=xf, min_step=ms)
+
+
+def rollout_f32(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int, model="srb"):
+    """The FP32 arithmetic reference (emul32.cpp): every model quantity rounded
+    to FP32, position, heading and linear velocity accumulated exactly, the
+    other state components rounded to FP32 each Euler step; node slopes
+    stored in FP32.  Same outputs as rollout() (diag aside) plus the control step of the
+    smallest per-step margin."""
+    return _templated(lib().orc_rollout_f32, model, veh, cst, ter, x0, ctrl, dt, n_sub)
+
+
+def rollout_templated(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int, model="srb"):
+    """The templated restatement (model.hpp) in plain FP64."""
+    return _templated(lib().orc_rollout_templated, model, veh, cst, ter, x0, ctrl, dt, n_sub)
+
+
+OP_FIELDS = ("euler_steps", "add", "mul", "div", "sqrt", "sin", "cos", "atan2", "asin")
+
+
+def count_ops(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int, model="srb"):
+    """Operations of the templated model's rollout of every candidate, summed
+    (additions count subtractions too), with the number of Euler steps run."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
+    H, N, _ = ctrl.shape
+    out = (C.c_long * 9)()
+    rc = lib().orc_count_ops(0 if model == "srb" else 1, C.byref(vehicle(veh)), C.byref(cost(cst)),
+                             C.byref(ter.c), _ptr(x0, _fp), 1 if x0.ndim == 2 else 0, _ptr(ctrl, _fp), N, H,
+                             float(dt), int(n_sub), out)
+    if rc != 0:
+        raise ValueError("operation count rejected its arguments")
+    return dict(zip(OP_FIELDS, [int(v) for v in out]))
 
 
 # ---- Extended single-track (EST) planar model --------------------------------

@@ -6,6 +6,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -78,3 +79,47 @@ def test_omp_threads_follows_the_environment(monkeypatch):
     assert bench.omp_threads() == 3
     monkeypatch.delenv("OMP_NUM_THREADS")
     assert bench.omp_threads() == len(os.sched_getaffinity(0))
+
+
+def _count(name):
+    import gen
+    import oracle
+    w = {"plain": gen.workload_plain, "scaled": gen.workload_scaled, "paper": gen.workload_paper}[name](0)
+    N = min(w.N, 1024)
+    x0 = w.x0[:N] if w.x0.ndim == 2 else w.x0
+    return oracle.count_ops(w.vehicle, w.cost, oracle.Terrain.of(w.terrain), x0, w.ctrl[:, :N], w.dt, w.n_sub)
+
+
+@pytest.mark.parametrize("name", ["plain", "scaled", "paper"])
+def test_roofline_flops_are_the_oracles_count(name):
+    """The roofline's numerator is the oracle's counted work per Euler step
+    (additions, subtractions, multiplications, divisions), not a hand count."""
+    c = _count(name)
+    n = c["euler_steps"]
+    assert abs((c["add"] + c["mul"] + c["div"]) / n - bench.FLOPS_PER_SUBSTEP[name]) < 5e-4
+    # the model's structure per Euler step (Sec. IV-A..IV-C): one slip angle
+    # per wheel; a tire square root per wheel and the goal test's; sines of
+    # the three angles and of the ESM's |phi| + phibar; cosines of the three
+    # angles, of each wheel's steering angle and of the pitch in the ESM
+    assert c["atan2"] == 4 * n
+    assert 5 * n <= c["sqrt"] <= 5 * n + 1024
+    assert 4 * n <= c["sin"] <= 4 * n + 1024
+    assert 8 * n <= c["cos"] <= 8 * n + 1024
+    assert c["div"] == 30 * n
+
+
+def test_flop_count_scales_with_the_horizon():
+    import gen
+    import oracle
+    w = gen.workload_plain(0, N=16, H=8)
+    t = oracle.Terrain.of(w.terrain)
+    a = oracle.count_ops(w.vehicle, w.cost, t, w.x0, w.ctrl, w.dt, w.n_sub)
+    b = oracle.count_ops(w.vehicle, w.cost, t, w.x0, np.concatenate([w.ctrl, w.ctrl]), w.dt, w.n_sub)
+    assert b["euler_steps"] == 2 * a["euler_steps"]
+    per_a = (a["add"] + a["mul"] + a["div"]) / a["euler_steps"]
+    per_b = (b["add"] + b["mul"] + b["div"]) / b["euler_steps"]
+    assert abs(per_a - per_b) < 2.0      # the terminal cost and liftoff branches aside
+
+
+def test_fp32_peak_from_unit_counts_and_clock():
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.54784) < 1e-9
