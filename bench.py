@@ -298,7 +298,8 @@ def run_paper_config(ctx, dev, stream, flush, peak, steps=10, warmup=3):
                               w.terrain.x0, w.terrain.y0)
     ctrl = torch.as_tensor(w.ctrl).to(dev)
     x0 = [float(v) for v in w.x0]
-    outs = ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False)
+    outs = ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False,
+                    want_best_margin=False)
     for _ in range(warmup):
         ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, out=outs)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -364,7 +365,8 @@ def run_variants(ctx, dev, stream, flush, steps=10):
                                 ws.terrain.x0, ws.terrain.y0, fmt=atp.BF16X4)
     ctrl16 = torch.as_tensor(ws.ctrl).to(dev)
     x016 = torch.as_tensor(np.ascontiguousarray(ws.x0.T)).to(dev)
-    o16 = ctx.plan(ws.vehicle, ws.cost, ter16, x016, ctrl16, ws.dt, ws.n_sub, want_candidates=False)
+    o16 = ctx.plan(ws.vehicle, ws.cost, ter16, x016, ctrl16, ws.dt, ws.n_sub, want_candidates=False,
+                   want_best_margin=False)
     ms = _time(lambda: ctx.plan(ws.vehicle, ws.cost, ter16, x016, ctrl16, ws.dt, ws.n_sub, out=o16),
                steps, 3, stream, flush)
     out["bf16_terrain_plan"] = {"workload": "the scaled plan on BF16 texels", "ms_per_plan": ms,
@@ -402,7 +404,7 @@ def run_variants(ctx, dev, stream, flush, steps=10):
     return out
 
 
-def run_serving(seconds, device):
+def run_serving(seconds, device, sweep_rates=(), sweep_seconds=10.0):
     """The serving stream: 32 vehicles, each on its own resident 512-2048^2
     tile, Poisson plan requests at 20 Hz per vehicle with N in {1k, 4k, 16k,
     32k}, H uniform in [40, 150], dt in {0.020, 0.025, ..., 0.050} s, warm
@@ -423,14 +425,35 @@ def run_serving(seconds, device):
     plain = srv.sequential(trace)
     gap_plain = srv.max_loop_gap
     same = all(a.best_idx == b.best_idx and a.best_cost == b.best_cost for a, b in zip(served, plain))
-    return {"workload": "32 vehicles x 20 Hz Poisson, N in {1024, 4096, 16384, 32768}, "
-                        "H 40-150, dt 0.02-0.05 s, own 512-2048^2 tile at 0.1 m, warm start",
-            "trace_s": seconds, "requests": len(trace),
-            "served": dict(serve.latency_summary(served),
-                           longest_loop_pause_ms=1000 * gap_served[0], at_s=gap_served[1]),
-            "plain_sequential": dict(serve.latency_summary(plain),
-                                     longest_request_ms=1000 * gap_plain[0], at_s=gap_plain[1]),
-            "identical_results": bool(same)}
+    out = {"workload": "32 vehicles x 20 Hz Poisson, N in {1024, 4096, 16384, 32768}, "
+                       "H 40-150, dt 0.02-0.05 s, own 512-2048^2 tile at 0.1 m, warm start",
+           "trace_s": seconds, "requests": len(trace),
+           "served": dict(serve.latency_summary(served),
+                          longest_loop_pause_ms=1000 * gap_served[0], at_s=gap_served[1]),
+           "plain_sequential": dict(serve.latency_summary(plain),
+                                    longest_request_ms=1000 * gap_plain[0], at_s=gap_plain[1]),
+           "identical_results": bool(same)}
+    # the same 32-vehicle mix at higher request rates, until the plain path
+    # falls behind: where continuous batching pays
+    sweep = []
+    for rate in sweep_rates:
+        tr = serve.poisson_trace(32, float(rate), sweep_seconds, seed=1000 + int(rate))
+        serve.reset_warm_start(vehicles)
+        a = srv.serve(tr)
+        serve.reset_warm_start(vehicles)
+        b = srv.sequential(tr)
+        sa, sb = serve.latency_summary(a), serve.latency_summary(b)
+        offered = sum(r.N * r.H for r in tr) / sweep_seconds
+        sweep.append({"rate_hz_per_vehicle": rate, "requests": len(tr), "offered_rollout_steps_per_s": offered,
+                      "served": {k: sa[k] for k in ("p50_ms", "p99_ms", "max_ms", "mean_batch",
+                                                   "rollout_steps_per_s")},
+                      "plain_sequential": {k: sb[k] for k in ("p50_ms", "p99_ms", "max_ms",
+                                                             "rollout_steps_per_s")},
+                      "identical_results": bool(all(x.best_idx == y.best_idx and x.best_cost == y.best_cost
+                                                    for x, y in zip(a, b)))})
+    if sweep:
+        out["rate_sweep"] = {"trace_s": sweep_seconds, "points": sweep}
+    return out
 
 
 def main():
@@ -443,8 +466,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4],
                     help="threads per candidate (ATP_OPT_LANES; 0 chooses by batch size)")
-    ap.add_argument("--serve-seconds", type=float, default=6.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="seconds of the 32-vehicle request stream (0: skip)")
+    ap.add_argument("--serve-rates", default="30,40,60,80",
+                    help="per-vehicle request rates (Hz) of the serving sweep, comma-separated ('' skips)")
+    ap.add_argument("--sweep-seconds", type=float, default=6.0, help="seconds of each sweep stream")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -471,7 +497,10 @@ def main():
     ctrl = torch.as_tensor(w.ctrl).to(dev)
     per = w.x0.ndim == 2
     x0 = torch.as_tensor(np.ascontiguousarray(w.x0.T)).to(dev) if per else [float(v) for v in w.x0]
-    outs = ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False)
+    # the planner's outputs: best controls, cost, minimum ESM margin and its step
+    # (the optional per-step margins of the best candidate are not asked for)
+    outs = ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, want_candidates=False,
+                    want_best_margin=False)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
@@ -596,7 +625,8 @@ def main():
             line["paper_configuration"] = run_paper_config(ctx, dev, stream, flush, peak)
             line["other_kernels"] = run_variants(ctx, dev, stream, flush)
         if args.serve_seconds > 0:
-            line["serving"] = run_serving(args.serve_seconds, local)
+            rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
+            line["serving"] = run_serving(args.serve_seconds, local, rates, args.sweep_seconds)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

@@ -207,7 +207,10 @@ int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *cos
  *   best_ctrl_dev float [H][2] or NULL: the best candidate's controls with the
  *                 steering rate clamped as used
  *   best_margin_dev float [H] or NULL: the best candidate's minimum U_ESM over
- *                 each control step (the final state folded into step H-1)
+ *                 each control step (the final state folded into step H-1);
+ *                 only then does the plan keep every candidate's per-step
+ *                 margins (4 N H bytes of scratch written), otherwise each
+ *                 candidate keeps just the step of its smallest margin
  *   cand_cost_dev, cand_margin_dev  float [N] or NULL: J and min U_ESM
  *   cand_flags_dev uint8 [N] or NULL: ATP_FLAG_* bits
  *   cand_xf_dev   float [13][N] or NULL: final states, SoA
@@ -278,11 +281,44 @@ int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
              const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int K, int H, float dt,
              int n_sub, int ckpt, float *cost_dev, float *grad_dev, void *stream);
 
+/* Constraint gradient: the same adjoint for each candidate's ESM margin, the
+ * minimum of U_ESM over every state of its trajectory (Sec. IV-B; the final
+ * state and the states frozen at the goal included, as atp_plan's margin):
+ * d(min U_ESM)/du, taken as the gradient of U_ESM at the state holding the
+ * minimum (the first such state on ties), a subgradient of the minimum.
+ *   margin_dev float [K]: each candidate's margin [J] (as atp_plan's)
+ *   grad_dev   float [H][K][2]: d(margin)/d(steering rate), d(margin)/d(accel)
+ * Other arguments, memory and limits as atp_grad. */
+int atp_grad_margin(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                    const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
+                    const float *ctrl_dev, int K, int H, float dt, int n_sub, int ckpt,
+                    float *margin_dev, float *grad_dev, void *stream);
+
+/* Gradient refinement of K candidates by projected gradient descent on
+ * their cost (atp_grad), in three calls per iteration; every array is
+ * device memory, [H][K][2] ones (steering rate, acceleration) 8-byte aligned:
+ *   atp_refine_init    eta[K] = step / (max over k, c of |grad[k][j][c]| + 1e-12)
+ *   atp_refine_trial   trial = ctrl - eta[j] grad, the steering rate clamped
+ *                      to +/- rate_max (the admissible set of Sec. IV-C)
+ *   atp_refine_accept  for each candidate whose trial_cost is finite and lower
+ *                      than cost: ctrl, grad and cost take the trial's and
+ *                      eta grows by 1.5; for the others eta halves.
+ * An iteration is trial, atp_grad on the trial, accept; the cost then never
+ * increases.  K, H >= 1; step > 0; rate_max >= 0. */
+int atp_refine_init(atp_ctx *ctx, const float *grad_dev, int K, int H, float step, float *eta_dev, void *stream);
+int atp_refine_trial(atp_ctx *ctx, const float *ctrl_dev, const float *grad_dev, const float *eta_dev, int K,
+                     int H, float rate_max, float *trial_dev, void *stream);
+int atp_refine_accept(atp_ctx *ctx, int K, int H, const float *trial_dev, const float *trial_cost_dev,
+                      const float *trial_grad_dev, float *ctrl_dev, float *cost_dev, float *grad_dev,
+                      float *eta_dev, void *stream);
+
 /* Candidate sampler (the on-GPU drawing of Sec. IV-D): writes float2
  * ctrl[H][N] with ctrl[k][j] = nominal[k] + (sigma_rate n1, sigma_acc n2),
- * where (n1, n2) is the Box-Muller pair of two 23-bit uniforms taken from the
- * top bits of the first two words of Philox4x64-10 (Salmon et al., SC'11) at
- * counter (j, k, nonce, 0) under key (key0, key1); candidate 0 is the nominal.
+ * where (n1, n2) is a Box-Muller pair of 23-bit uniforms from Philox4x64-10
+ * (Salmon et al., SC'11) under key (key0, key1): one call at counter
+ * (j, kq, nonce, 0) serves steps k = 4 kq + s, s = 0..3, with the words
+ * (w0, w1) for s = 0, 2 and (w2, w3) for s = 1, 3, each word's bits 63..41
+ * for s < 2 and bits 31..9 for s >= 2; candidate 0 is the nominal.
  * The nominal is a warm start from the previous plan's best controls,
  * nominal[k] = prev_best[min(k + shift, H_prev - 1)] (float [H_prev][2],
  * device), or zero when H_prev = 0.  Draws depend only on (key, nonce, j, k),
@@ -368,17 +404,22 @@ int atp_costmap(atp_ctx *ctx, const double *xy_dev, const int *start, const int 
  * a plugin host that gives its plugins no allocator.  The paper has no
  * counterpart; it exists for such callers only.
  *
- * Arguments, outputs and results are those of atp_plan, without a context.
- * Its scratch is one file-scope device array of 8 MiB in this library, which
- * every GPU that loads the library holds until the process exits.  It
- * supports plans whose scratch (256 B + 9 N bytes + 4 N H bytes, each part
- * rounded up to 256 B) fits in 8 MiB, e.g. N = 16384 with H <= 125; larger
- * plans return ATP_ERR_UNSUPPORTED before anything is enqueued.  The call
+ * Arguments, outputs and results are those of atp_plan on a context with the
+ * default options (running cost accumulated in FP32, threads per candidate
+ * chosen by batch size), without a context.  Its scratch is one file-scope
+ * device array of 8 MiB in this library, which every GPU that loads the
+ * library holds until the process exits.  It supports plans whose scratch
+ * fits in 8 MiB: 256 B + 13 N bytes, plus 4 N H bytes when best_margin_dev
+ * is given, each of the five parts rounded up to 256 B (N up to about
+ * 645,000 without per-step margins; N = 16384 with H <= 124 with them);
+ * larger plans return ATP_ERR_UNSUPPORTED before anything is enqueued.  The call
  * runs on the calling thread's current device (at most device 63), calls no
  * cudaMalloc or cudaFree, and enqueues two small memsets that reset the
  * reduction state before the kernel.  Its first call on a device looks up the
  * array's device address with that device current (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call shares the one
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: a caller that resets a device (cudaDeviceReset)
+ * must not call this function on that device afterwards.  Every call shares the one
  * array, so calls that overlap on the GPU (other streams, other host threads)
  * race and corrupt each other's results: serialise them. */
 int atp_plan_noalloc(const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,

@@ -123,6 +123,10 @@ def lib():
                                          _fp, C.c_int, _fp, C.c_int, C.c_int, C.c_double, C.c_int,
                                          _dp, _dp]
             L.orc_grad_batch.restype = C.c_int
+            L.orc_grad_margin_batch.argtypes = L.orc_grad_batch.argtypes
+            L.orc_grad_margin_batch.restype = C.c_int
+            L.orc_margin_f64.argtypes = L.orc_cost_f64.argtypes
+            L.orc_margin_f64.restype = C.c_double
             L.orc_est_rotation.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
             L.orc_est_eval.argtypes = [C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(_Terrain),
                                        _dp, _dp, _dp, _dp]
@@ -379,6 +383,30 @@ def grad(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int):
     if rc != 0:
         raise ValueError("oracle grad rejected its arguments")
     return J, G
+
+
+def grad_margin(veh: dict, cst: dict, ter: Terrain, x0, ctrl, dt: float, n_sub: int):
+    """ESM margin [N] (min U_ESM over each trajectory) and d(margin)/du
+    [H, N, 2] by FP64 reverse-mode AD (adjoint.cpp)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float32)
+    ctrl = np.ascontiguousarray(ctrl, dtype=np.float32)
+    H, N, _ = ctrl.shape
+    M = np.empty(N)
+    G = np.empty((H, N, 2))
+    rc = lib().orc_grad_margin_batch(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                                     _ptr(x0, _fp), 1 if x0.ndim == 2 else 0, _ptr(ctrl, _fp), N, H,
+                                     float(dt), int(n_sub), _ptr(M, _dp), _ptr(G, _dp))
+    if rc != 0:
+        raise ValueError("oracle margin gradient rejected its arguments")
+    return M, G
+
+
+def margin_f64(veh: dict, cst: dict, ter: Terrain, x0, u, dt: float, n_sub: int):
+    """The ESM margin of one candidate with FP64 controls u [H, 2]."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_margin_f64(C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(ter.c),
+                                _ptr(x0, _dp), _ptr(u, _dp), u.shape[0], float(dt), int(n_sub))
 
 
 def cost_f64(veh: dict, cst: dict, ter: Terrain, x0, u, dt: float, n_sub: int):

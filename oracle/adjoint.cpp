@@ -118,20 +118,24 @@ double orc_cost_f64(const orc_vehicle *v, const orc_cost *c, const orc_terrain *
     return costT<double>(v, c, t, x0, u, H, dt, n_sub);
 }
 
-// J and dJ/du (grad[H][2]) of one candidate by reverse-mode AD on a tape
-double orc_grad(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const double x0[13],
-                const float *ctrl, int H, double dt, int n_sub, double *grad)
+// The objective (0: J; 1: the ESM margin, min U_ESM over the trajectory) of
+// one candidate and its gradient grad[H][2] by reverse-mode AD on a tape.  The
+// margin's minimum is taken by value (the first state holding it), so the tape
+// records the subgradient through that state.
+static double tape_grad(int objective, const orc_vehicle *v, const orc_cost *c, const orc_terrain *t,
+                        const double x0[13], const float *ctrl, int H, double dt, int n_sub, double *grad)
 {
     Tape tape;
     tape.val.reserve(1 << 20);
     g_tape = &tape;
     std::vector<AD> u(2 * (size_t)H);
     for (int i = 0; i < 2 * H; ++i) u[i] = AD((double)ctrl[i], tape.node((double)ctrl[i]));
-    AD J = costT<AD>(v, c, t, x0, u.data(), H, dt, n_sub);
+    const orcm::Result<AD> r = orcm::rolloutT<AD, AD>(v, c, t, x0, u.data(), H, dt, n_sub);
+    const AD f = objective == 0 ? r.J : r.margin;
     std::vector<double> adj(tape.val.size(), 0.0);
-    if (J.i >= 0) {
-        adj[J.i] = 1.0;
-        for (int n = J.i; n >= 0; --n) {
+    if (f.i >= 0) {
+        adj[f.i] = 1.0;
+        for (int n = f.i; n >= 0; --n) {
             if (adj[n] == 0.0) continue;
             if (tape.pa[n] >= 0) adj[tape.pa[n]] += adj[n] * tape.da[n];
             if (tape.pb[n] >= 0) adj[tape.pb[n]] += adj[n] * tape.db[n];
@@ -139,13 +143,21 @@ double orc_grad(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, c
     }
     for (int i = 0; i < 2 * H; ++i) grad[i] = adj[u[i].i];
     g_tape = nullptr;
-    return J.v;
+    return f.v;
 }
 
-// J and gradients of N candidates (ctrl [H][N][2], x0 [N][13] or shared [13]), OpenMP over candidates
-int orc_grad_batch(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const float *x0,
-                   int x0_per_cand, const float *ctrl, int N, int H, double dt, int n_sub, double *J,
-                   double *grad)
+// J and dJ/du (grad[H][2]) of one candidate by reverse-mode AD on a tape
+double orc_grad(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const double x0[13],
+                const float *ctrl, int H, double dt, int n_sub, double *grad)
+{
+    return tape_grad(0, v, c, t, x0, ctrl, H, dt, n_sub, grad);
+}
+
+// The objective (0: J; 1: the margin) and its gradient for N candidates
+// (ctrl [H][N][2], x0 [N][13] or shared [13]), OpenMP over candidates.
+static int grad_batch(int objective, const orc_vehicle *v, const orc_cost *c, const orc_terrain *t,
+                      const float *x0, int x0_per_cand, const float *ctrl, int N, int H, double dt, int n_sub,
+                      double *F, double *grad)
 {
     if (N <= 0 || H <= 0 || n_sub <= 0 || !(dt > 0.0)) return -1;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -159,13 +171,36 @@ int orc_grad_batch(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t
             uj[2 * k] = ctrl[((size_t)k * N + j) * 2];
             uj[2 * k + 1] = ctrl[((size_t)k * N + j) * 2 + 1];
         }
-        J[j] = orc_grad(v, c, t, xs, uj.data(), H, dt, n_sub, gj.data());
+        F[j] = tape_grad(objective, v, c, t, xs, uj.data(), H, dt, n_sub, gj.data());
         for (int k = 0; k < H; ++k) {
             grad[((size_t)k * N + j) * 2] = gj[2 * k];
             grad[((size_t)k * N + j) * 2 + 1] = gj[2 * k + 1];
         }
     }
     return 0;
+}
+
+int orc_grad_batch(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const float *x0,
+                   int x0_per_cand, const float *ctrl, int N, int H, double dt, int n_sub, double *J,
+                   double *grad)
+{
+    return grad_batch(0, v, c, t, x0, x0_per_cand, ctrl, N, H, dt, n_sub, J, grad);
+}
+
+// the ESM margin (min U_ESM over the trajectory) and d(margin)/du
+int orc_grad_margin_batch(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const float *x0,
+                          int x0_per_cand, const float *ctrl, int N, int H, double dt, int n_sub,
+                          double *margin, double *grad)
+{
+    return grad_batch(1, v, c, t, x0, x0_per_cand, ctrl, N, H, dt, n_sub, margin, grad);
+}
+
+// the margin of one candidate in plain FP64 with FP64 controls u[H][2]
+// (central finite differences)
+double orc_margin_f64(const orc_vehicle *v, const orc_cost *c, const orc_terrain *t, const double x0[13],
+                      const double *u, int H, double dt, int n_sub)
+{
+    return orcm::rolloutT<double, double>(v, c, t, x0, u, H, dt, n_sub).margin;
 }
 
 }  // extern "C"

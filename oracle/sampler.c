@@ -52,11 +52,21 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
     memcpy(out, c, sizeof c);
 }
 
+/* 23-bit uniform on (0, 1) from the high (bits 63..41) or low (bits 31..9)
+ * half of a 64-bit Philox word */
+static double unif23(uint64_t w, int low)
+{
+    uint64_t b = low ? (w >> 9) & 0x7FFFFFull : w >> 41;
+    return ((double)b + 0.5) * (1.0 / 8388608.0);
+}
+
 /* Candidate controls ctrl[k][j] = nominal[k] + (sigma_rate n1, sigma_acc n2)
- * with (n1, n2) the Box-Muller pair of the two 23-bit uniforms taken from the
- * top bits of the first two Philox words at counter (j, k, nonce, 0);
- * candidate 0 is the nominal itself.  nominal[k] is the warm start
- * prev[min(k + shift, H_prev - 1)] (zero when H_prev = 0). */
+ * with (n1, n2) a Box-Muller pair of 23-bit uniforms.  One Philox call at
+ * counter (j, kq, nonce, 0) serves the four steps k = 4 kq + s, s = 0..3: its
+ * words (w0, w1) for s = 0 and 2, (w2, w3) for s = 1 and 3, their high
+ * halves for s < 2 and their low halves for s >= 2.  Candidate 0 is the
+ * nominal itself.  nominal[k] is the warm start prev[min(k + shift,
+ * H_prev - 1)] (zero when H_prev = 0). */
 void orc_sample(const float *prev, int H_prev, int shift, double sigma_rate, double sigma_acc,
                 uint64_t key0, uint64_t key1, uint64_t nonce, int N, int H, double *out)
 {
@@ -76,11 +86,12 @@ void orc_sample(const float *prev, int H_prev, int shift, double sigma_rate, dou
                 o[0] = nom[0];
                 o[1] = nom[1];
             } else {
-                uint64_t ctr[4] = { (uint64_t)j, (uint64_t)k, nonce, 0 }, w[4];
+                uint64_t ctr[4] = { (uint64_t)j, (uint64_t)(k / 4), nonce, 0 }, w[4];
+                int s = k % 4, low = s >= 2;
                 double u1, u2, r;
                 orc_philox4x64_10(ctr, key, w);
-                u1 = ((double)(w[0] >> 41) + 0.5) * (1.0 / 8388608.0);
-                u2 = ((double)(w[1] >> 41) + 0.5) * (1.0 / 8388608.0);
+                u1 = unif23((s & 1) ? w[2] : w[0], low);
+                u2 = unif23((s & 1) ? w[3] : w[1], low);
                 r = sqrt(-2.0 * log(u1));
                 o[0] = nom[0] + sigma_rate * r * cos(2.0 * M_PI * u2);
                 o[1] = nom[1] + sigma_acc * r * sin(2.0 * M_PI * u2);

@@ -29,8 +29,9 @@ TERRAIN_HAS_COSTMAP = 1
 EXPORTS = ("atp_version", "atp_create", "atp_destroy", "atp_last_error", "atp_reserve",
            "atp_terrain_bytes", "atp_terrain_prepare", "atp_plan", "atp_rollout",
            "atp_plan_noalloc", "atp_math_check", "atp_sample", "atp_plan_batch",
-           "atp_set_option", "atp_grad", "atp_plan_est", "atp_lod_smooth", "atp_costmap",
-           "atp_plan_lanes")
+           "atp_set_option", "atp_grad", "atp_grad_margin", "atp_plan_est", "atp_lod_smooth",
+           "atp_costmap", "atp_plan_lanes", "atp_refine_init", "atp_refine_trial",
+           "atp_refine_accept")
 
 
 class Vehicle(C.Structure):
@@ -117,6 +118,10 @@ def load(build_if_missing: bool = True):
         L.atp_grad.argtypes = [_vp, C.POINTER(Vehicle), C.POINTER(Cost), C.POINTER(TerrainC),
                                C.POINTER(State), _vp, _vp, C.c_int, C.c_int, C.c_float, C.c_int,
                                C.c_int, _vp, _vp, _vp]
+        L.atp_grad_margin.argtypes = L.atp_grad.argtypes
+        L.atp_refine_init.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_float, _vp, _vp]
+        L.atp_refine_trial.argtypes = [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_float, _vp, _vp]
+        L.atp_refine_accept.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.atp_sample.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_int, C.c_int, _vp, _vp]
         L.atp_plan_lanes.argtypes = [_vp, C.c_int]
@@ -224,10 +229,12 @@ class Context:
         return Terrain(tex, h)
 
     def plan(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0, out=None,
-             stream=None, want_candidates=True, want_xf=False):
+             stream=None, want_candidates=True, want_xf=False, want_best_margin=True):
         """Plan over ctrl (float32 CUDA [H, N, 2]).  x0: 13 floats (host) or a
         float32 CUDA tensor [13, N] of per-candidate states.  Returns a dict of
-        CUDA tensors; nothing is synchronized."""
+        CUDA tensors; nothing is synchronized.  Without want_best_margin the
+        best candidate's per-step margins are not produced (and no candidate's
+        per-step margins are kept)."""
         import torch
         H, N, _ = ctrl.shape
         dev = ctrl.device
@@ -235,7 +242,8 @@ class Context:
         if "out" not in o:
             o["out"] = torch.zeros(6, dtype=torch.int32, device=dev)
             o["best_ctrl"] = torch.empty((H, 2), dtype=torch.float32, device=dev)
-            o["best_margin"] = torch.empty(H, dtype=torch.float32, device=dev)
+            if want_best_margin:
+                o["best_margin"] = torch.empty(H, dtype=torch.float32, device=dev)
             if want_candidates:
                 o["cost"] = torch.empty(N, dtype=torch.float32, device=dev)
                 o["margin"] = torch.empty(N, dtype=torch.float32, device=dev)
@@ -341,19 +349,37 @@ class Context:
         return [q["out"] for q in requests]
 
     def grad(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0, ckpt=10,
-             stream=None):
-        """J [K] and dJ/dctrl [H, K, 2] of K candidates (atp_grad)."""
+             stream=None, objective="cost"):
+        """J [K] and dJ/dctrl [H, K, 2] of K candidates (atp_grad), or with
+        objective="margin" each candidate's ESM margin and its gradient
+        (atp_grad_margin)."""
         import torch
         H, K, _ = ctrl.shape
         J = torch.empty(K, dtype=torch.float32, device=ctrl.device)
         G = torch.empty((H, K, 2), dtype=torch.float32, device=ctrl.device)
         xs, xdev = (None, x0) if isinstance(x0, torch.Tensor) else (state(x0), None)
-        rc = self.lib.atp_grad(self.h, C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(terrain.c),
-                               C.byref(xs) if xs is not None else None, _ptr(xdev), _ptr(ctrl),
-                               int(K), int(H), float(dt), int(n_sub), int(ckpt), _ptr(J), _ptr(G),
-                               _stream(stream))
-        self._check(rc, "atp_grad")
+        fn = {"cost": self.lib.atp_grad, "margin": self.lib.atp_grad_margin}[objective]
+        rc = fn(self.h, C.byref(vehicle(veh)), C.byref(cost(cst)), C.byref(terrain.c),
+                C.byref(xs) if xs is not None else None, _ptr(xdev), _ptr(ctrl),
+                int(K), int(H), float(dt), int(n_sub), int(ckpt), _ptr(J), _ptr(G), _stream(stream))
+        self._check(rc, "atp_grad" if objective == "cost" else "atp_grad_margin")
         return J, G
+
+    def refine_init(self, grad, step, eta, stream=None):
+        H, K, _ = grad.shape
+        self._check(self.lib.atp_refine_init(self.h, _ptr(grad), int(K), int(H), float(step), _ptr(eta),
+                                             _stream(stream)), "atp_refine_init")
+
+    def refine_trial(self, ctrl, grad, eta, rate_max, trial, stream=None):
+        H, K, _ = ctrl.shape
+        self._check(self.lib.atp_refine_trial(self.h, _ptr(ctrl), _ptr(grad), _ptr(eta), int(K), int(H),
+                                              float(rate_max), _ptr(trial), _stream(stream)), "atp_refine_trial")
+
+    def refine_accept(self, trial, trial_cost, trial_grad, ctrl, cost, grad, eta, stream=None):
+        H, K, _ = ctrl.shape
+        self._check(self.lib.atp_refine_accept(self.h, int(K), int(H), _ptr(trial), _ptr(trial_cost),
+                                               _ptr(trial_grad), _ptr(ctrl), _ptr(cost), _ptr(grad), _ptr(eta),
+                                               _stream(stream)), "atp_refine_accept")
 
     def sample(self, N, H, sigma_rate, sigma_acc, key, nonce, prev=None, shift=1, out=None,
                stream=None):

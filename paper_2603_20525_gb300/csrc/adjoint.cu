@@ -1,6 +1,10 @@
-// adjoint.cu - hand-written reverse-mode adjoint of the discrete rollout cost
-// (arxiv 2603.20525, Sec. IV-A..IV-C): dJ/du for the raw control sequence u
-// of each of K candidates, J = sum over Euler steps of h L + Phi.
+// adjoint.cu - hand-written reverse-mode adjoint of the discrete rollout
+// (arxiv 2603.20525, Sec. IV-A..IV-C): the gradient, with respect to the raw
+// control sequence u of each of K candidates, of its cost J = sum over Euler
+// steps of h L + Phi, or of its ESM margin, the minimum of U_ESM over every
+// state of the trajectory (Sec. IV-B; the constraint the soft cost guards).
+// The margin's gradient is that of U_ESM at the state holding the minimum
+// (the first one on ties), as a subgradient of the minimum.
 //
 // Four threads per candidate, one wheel each, as in the plan kernel's
 // four-lane layout: every lane repeats the body arithmetic and its adjoint
@@ -343,6 +347,8 @@ __device__ __forceinline__ StepOut step_fwd(const GradParams &p, St &s, float dd
 __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, float lam[13], float &g_dd,
                          float &g_ax, const Lane &ln)
 {
+    // the running cost enters the cost's adjoint only
+    const float cw = p.objective == kGradCost ? 1.f : 0.f;
     const Veh &V = p.V;
     const Cost &Cc = p.C;
     const Terrain &T = p.T;
@@ -399,10 +405,10 @@ __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, f
     const float a_dwx = h * lam[9], a_dwy = h * lam[10], a_dwz = h * lam[11];
     if (!d_clamped) g_dd += h * lam[12];
     // running cost: J += h L, L = wt + wc dd^2 + sigma soft^2 + sum of costmap
-    g_dd += h * 2.f * Cc.wc * dd;
+    g_dd += cw * (h * 2.f * Cc.wc * dd);
     float a_U = 0.f;
-    if (soft > 0.f) a_U = -h * 2.f * Cc.sigma * soft * Cc.inv_eps;
-    const float a_csum = h;
+    if (soft > 0.f) a_U = cw * (-h * 2.f * Cc.sigma * soft * Cc.inv_eps);
+    const float a_csum = cw * h;
     // positions: d(x,y,z) = R v
     float a_sph = 0.f, a_cph = 0.f, a_sth = 0.f, a_cth = 0.f, a_sps = 0.f, a_cps = 0.f;
     ad.R[0] += a_dx * vx; ad.R[1] += a_dx * vy; ad.R[2] += a_dx * vz;
@@ -521,6 +527,33 @@ __device__ void step_adj(const GradParams &p, const St &s, float dd, float ax, f
     lam[12] = a_d;
 }
 
+// U_ESM of a state (Sec. IV-B), as the plan kernel evaluates it
+__device__ __forceinline__ float state_esm(const Veh &V, const St &s)
+{
+    float sth, cth, sph, cph;
+    sincos_r(s.th, sth, cth);
+    sincos_r(s.ph, sph, cph);
+    return esm(V, s.ph, sph, cph, cth);
+}
+
+// lam += dU_ESM/d(state) at the state s: U = +/- M g Rbar (1 - (sin|phi|
+// cos phibar + cos phi sin phibar)) cos theta depends on theta and phi only
+__device__ __forceinline__ void esm_adj(const Veh &V, const St &s, float lam[13])
+{
+    float sth, cth, sph, cph;
+    sincos_r(s.th, sth, cth);
+    sincos_r(s.ph, sph, cph);
+    const float sg = fabsf(s.ph) < V.tip ? 1.f : -1.f;
+    const float sabs = s.ph < 0.f ? -sph : sph;
+    const float sv = fmaf(sabs, V.cpb, cph * V.spb);
+    const float a_s = -V.MgRbar * cth * sg;
+    const float a_cth = V.MgRbar * (1.f - sv) * sg;
+    const float a_sph = (s.ph < 0.f ? -1.f : 1.f) * a_s * V.cpb;
+    const float a_cph = a_s * V.spb;
+    lam[4] -= a_cth * sth;
+    lam[5] += a_sph * cph - a_cph * sph;
+}
+
 __global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ GradParams p)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -553,8 +586,11 @@ __global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ Gra
     const int n_seg = (p.H + p.ckpt - 1) / p.ckpt;
     float *ck = p.ckpt_buf + tid;                 // [n_seg][20][K lanes]
     float *seg = p.seg_buf + tid;                 // [ckpt * n_sub][20][K lanes]
-    // forward: cost and checkpoints
+    // forward: cost (or margin) and checkpoints
+    const bool want_margin = p.objective == kGradMargin;
     float J = 0.f;
+    float Umin = CUDART_INF_F;                   // the margin: min U_ESM over the states
+    int emin = 0;                                // index of the state holding it (first on ties)
     bool done = false;
     int done_step = p.H * p.n_sub;               // Euler step index where the goal stopped the rollout
     for (int k = 0; k < p.H; ++k) {
@@ -562,6 +598,13 @@ __global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ Gra
         const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
         const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
         for (int q = 0; q < p.n_sub && !done; ++q) {
+            if (want_margin) {
+                const float U = state_esm(p.V, s);
+                if (U < Umin) {
+                    Umin = U;
+                    emin = k * p.n_sub + q;
+                }
+            }
             const StepOut o = step_fwd(p, s, dd, u.y, ln);
             if (!o.stepped) {
                 done = true;
@@ -571,18 +614,29 @@ __global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ Gra
             J = fmaf(p.h, o.L, J);
         }
     }
-    // terminal cost and its gradient
-    const float gdx = (s.x - Cc.gx_hi) + (s.xl - Cc.gx_lo);
-    const float gdy = (s.y - Cc.gy_hi) + (s.yl - Cc.gy_lo);
-    const float dist = sqrtf(fmaf(gdx, gdx, gdy * gdy));
-    J = fmaf(Cc.wg, dist, J);
-    if (ln.q == 0) p.cost[j] = J;
+    // terminal cost and its gradient, or the final state's share of the margin
     float lam[13];
 #pragma unroll
     for (int c = 0; c < 13; ++c) lam[c] = 0.f;
-    if (dist > 0.f) {
-        lam[0] = Cc.wg * gdx / dist;
-        lam[1] = Cc.wg * gdy / dist;
+    if (want_margin) {
+        const int e_final = done ? done_step : p.H * p.n_sub;
+        const float U = state_esm(p.V, s);
+        if (U < Umin) {
+            Umin = U;
+            emin = e_final;
+        }
+        if (emin == e_final) esm_adj(p.V, s, lam);
+        if (ln.q == 0) p.cost[j] = Umin;
+    } else {
+        const float gdx = (s.x - Cc.gx_hi) + (s.xl - Cc.gx_lo);
+        const float gdy = (s.y - Cc.gy_hi) + (s.yl - Cc.gy_lo);
+        const float dist = sqrtf(fmaf(gdx, gdx, gdy * gdy));
+        J = fmaf(Cc.wg, dist, J);
+        if (ln.q == 0) p.cost[j] = J;
+        if (dist > 0.f) {
+            lam[0] = Cc.wg * gdx / dist;
+            lam[1] = Cc.wg * gdy / dist;
+        }
     }
     // reverse, one checkpointed segment at a time
     for (int sg = n_seg - 1; sg >= 0; --sg) {
@@ -615,6 +669,8 @@ __global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ Gra
                 St r2;
                 st_load(seg + (size_t)local * kStFloats * KL, KL, r2);
                 step_adj(p, r2, dd, u.y, lam, g_dd, g_ax, ln);
+                // lam is now the adjoint of the step's start state
+                if (want_margin && e == emin) esm_adj(p.V, r2, lam);
             }
             // the steering rate is clamped to +/- its limit before use
             if (ln.q == 0) {

@@ -9,6 +9,8 @@ namespace atp {
 
 // threads per candidate in the adjoint (one wheel each)
 constexpr int kGradLanes = 4;
+// what the adjoint differentiates
+constexpr int kGradCost = 0, kGradMargin = 1;
 
 struct GradParams {
     Veh V;
@@ -19,7 +21,8 @@ struct GradParams {
     const float2 *ctrl;       // [H][K]
     int K, H, n_sub, ckpt;
     float h;
-    float *cost;              // [K]
+    int objective;            // kGradCost: J; kGradMargin: min U_ESM over the trajectory
+    float *cost;              // [K] the objective's value
     float *grad;              // [H][K][2]
     float *ckpt_buf;          // [ceil(H / ckpt)][20][K * kGradLanes]
     float *seg_buf;           // [ckpt * n_sub][20][K * kGradLanes]

@@ -14,6 +14,7 @@
 #include "adjoint.cuh"
 #include "est_kernel.cuh"
 #include "plan_kernel.cuh"
+#include "refine.cuh"
 #include "sampler.cuh"
 #include "terrain_tools.cuh"
 
@@ -68,42 +69,35 @@ bool fin(double v) { return std::isfinite(v); }
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-struct ScratchLayout {
-    size_t cost, margin, flags, step_margin, total;
+// Per-plan scratch: the candidates' cost, margin, flags and minimum-margin
+// step, and, only when the best candidate's per-step margins are asked for,
+// every candidate's per-step margins [H][N].
+struct RegionLayout {
+    size_t cost, margin, flags, min_step, step_margin, total;
 };
 
-ScratchLayout layout(size_t N, size_t H)
+RegionLayout region_layout(size_t N, size_t H, bool steps, size_t o = 0)
 {
-    ScratchLayout L;
-    size_t o = align_up(sizeof(atp::Scratch));
+    RegionLayout L;
     L.cost = o;        o = align_up(o + N * sizeof(float));
     L.margin = o;      o = align_up(o + N * sizeof(float));
     L.flags = o;       o = align_up(o + N);
-    L.step_margin = o; o = align_up(o + N * H * sizeof(float));
+    L.min_step = o;    o = align_up(o + N * sizeof(int));
+    L.step_margin = o; o = align_up(o + (steps ? N * H * sizeof(float) : 0));
     L.total = o;
     return L;
+}
+
+// Scratch of atp_plan_noalloc: one reduction header, then one plan's region.
+RegionLayout layout(size_t N, size_t H, bool steps)
+{
+    return region_layout(N, H, steps, align_up(sizeof(atp::Scratch)));
 }
 
 // Context scratch: kMaxBatch reduction headers at fixed offsets (each plan's
 // last CTA restores its header, so they stay valid across calls), then one
 // region per plan of the call.
 constexpr size_t kHeaderBytes = (atp::kMaxBatch * sizeof(atp::Scratch) + kAlign - 1) / kAlign * kAlign;
-
-struct RegionLayout {
-    size_t cost, margin, flags, step_margin, total;
-};
-
-RegionLayout region_layout(size_t N, size_t H)
-{
-    RegionLayout L;
-    size_t o = 0;
-    L.cost = o;        o = align_up(o + N * sizeof(float));
-    L.margin = o;      o = align_up(o + N * sizeof(float));
-    L.flags = o;       o = align_up(o + N);
-    L.step_margin = o; o = align_up(o + N * H * sizeof(float));
-    L.total = o;
-    return L;
-}
 
 int ensure_scratch_bytes(atp_ctx *ctx, size_t need)
 {
@@ -131,9 +125,9 @@ int ensure_scratch_bytes(atp_ctx *ctx, size_t need)
     return ATP_OK;
 }
 
-int ensure_scratch(atp_ctx *ctx, int N, int H)
+int ensure_scratch(atp_ctx *ctx, int N, int H, bool steps)
 {
-    return ensure_scratch_bytes(ctx, region_layout((size_t)N, (size_t)H).total);
+    return ensure_scratch_bytes(ctx, region_layout((size_t)N, (size_t)H, steps).total);
 }
 
 int check_vehicle(atp_ctx *ctx, const atp_vehicle *v)
@@ -331,7 +325,7 @@ int atp_create(atp_ctx **out, int device)
         delete ctx;
         return ATP_ERR_NOMEM;
     }
-    int rc = ensure_scratch(ctx, 1, 1);
+    int rc = ensure_scratch(ctx, 1, 1, true);
     if (rc != ATP_OK) {
         cudaFree(ctx->cm_box);
         delete ctx->batch;
@@ -364,8 +358,8 @@ int atp_reserve(atp_ctx *ctx, int N, int H)
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
     // room for any batch of up to kMaxBatch plans within these totals: each
     // plan's four arrays round up to kAlign at most once
-    return ensure_scratch_bytes(ctx, region_layout((size_t)N, (size_t)H).total +
-                                         (size_t)atp::kMaxBatch * 4 * kAlign);
+    return ensure_scratch_bytes(ctx, region_layout((size_t)N, (size_t)H, true).total +
+                                         (size_t)atp::kMaxBatch * 5 * kAlign);
 }
 
 size_t atp_terrain_bytes(int nx, int ny, int format)
@@ -444,8 +438,9 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     if (!out_dev) return fail(ctx, ATP_ERR_INVALID, "out_dev is NULL");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
-    if ((rc = ensure_scratch(ctx, N, H)) != ATP_OK) return rc;
-    const RegionLayout L = region_layout((size_t)N, (size_t)H);
+    const bool steps = best_margin_dev != nullptr;
+    if ((rc = ensure_scratch(ctx, N, H, steps)) != ATP_OK) return rc;
+    const RegionLayout L = region_layout((size_t)N, (size_t)H, steps);
     char *base = (char *)ctx->scratch + kHeaderBytes;
     atp::PlanParams p;
     std::memset(&p, 0, sizeof p);
@@ -455,7 +450,8 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     p.margin = cand_margin_dev ? cand_margin_dev : (float *)(base + L.margin);
     p.flags = cand_flags_dev ? cand_flags_dev : (uint8_t *)(base + L.flags);
     p.xf = cand_xf_dev;
-    p.step_margin = (float *)(base + L.step_margin);
+    p.min_step = (int *)(base + L.min_step);
+    p.step_margin = steps ? (float *)(base + L.step_margin) : nullptr;
     p.out = out_dev;
     p.best_ctrl = best_ctrl_dev;
     p.best_margin = best_margin_dev;
@@ -523,7 +519,7 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         }
         if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
         if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
-        need += region_layout((size_t)q.N, (size_t)q.H).total;
+        need += region_layout((size_t)q.N, (size_t)q.H, q.best_margin_dev != nullptr).total;
         // four lanes sum in another order, so a plan keeps its own layout's
         // four; two lanes give one lane's bits and are decided below
         lanes[r] = atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1;
@@ -553,7 +549,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
     char *region = (char *)ctx->scratch + kHeaderBytes;
     for (int r = 0; r < n_req; ++r) {
         const atp_plan_request &q = reqs[r];
-        const RegionLayout L = region_layout((size_t)q.N, (size_t)q.H);
+        const bool steps = q.best_margin_dev != nullptr;
+        const RegionLayout L = region_layout((size_t)q.N, (size_t)q.H, steps);
         atp::PlanParams &p = b.req[r];
         std::memset(&p, 0, sizeof p);
         derive(*q.veh, *q.cost, *q.terrain, p);
@@ -562,7 +559,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         p.margin = q.cand_margin_dev ? q.cand_margin_dev : (float *)(region + L.margin);
         p.flags = q.cand_flags_dev ? q.cand_flags_dev : (uint8_t *)(region + L.flags);
         p.xf = q.cand_xf_dev;
-        p.step_margin = (float *)(region + L.step_margin);
+        p.min_step = (int *)(region + L.min_step);
+        p.step_margin = steps ? (float *)(region + L.step_margin) : nullptr;
         p.out = q.out_dev;
         p.best_ctrl = q.best_ctrl_dev;
         p.best_margin = q.best_margin_dev;
@@ -592,8 +590,9 @@ extern "C" int atp_plan_est(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost
     if (!out_dev) return fail(ctx, ATP_ERR_INVALID, "out_dev is NULL");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
-    if ((rc = ensure_scratch(ctx, N, H)) != ATP_OK) return rc;
-    const RegionLayout L = region_layout((size_t)N, (size_t)H);
+    const bool steps = best_margin_dev != nullptr;
+    if ((rc = ensure_scratch(ctx, N, H, steps)) != ATP_OK) return rc;
+    const RegionLayout L = region_layout((size_t)N, (size_t)H, steps);
     char *base = (char *)ctx->scratch + kHeaderBytes;
     atp::PlanParams p;
     std::memset(&p, 0, sizeof p);
@@ -616,7 +615,8 @@ extern "C" int atp_plan_est(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost
     p.margin = cand_margin_dev ? cand_margin_dev : (float *)(base + L.margin);
     p.flags = cand_flags_dev ? cand_flags_dev : (uint8_t *)(base + L.flags);
     p.xf = cand_xf_dev;
-    p.step_margin = (float *)(base + L.step_margin);
+    p.min_step = (int *)(base + L.min_step);
+    p.step_margin = steps ? (float *)(base + L.step_margin) : nullptr;
     p.out = out_dev;
     p.best_ctrl = best_ctrl_dev;
     p.best_margin = best_margin_dev;
@@ -701,10 +701,11 @@ extern "C" int atp_costmap(atp_ctx *ctx, const double *xy_dev, const int *start,
     return ATP_OK;
 }
 
-extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
-                        const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
-                        const float *ctrl_dev, int K, int H, float dt, int n_sub, int ckpt,
-                        float *cost_dev, float *grad_dev, void *stream)
+namespace {
+
+int grad_impl(atp_ctx *ctx, int objective, const atp_vehicle *veh, const atp_cost *cost,
+              const atp_terrain *terrain, const atp_state *x0, const float *x0_dev, const float *ctrl_dev,
+              int K, int H, float dt, int n_sub, int ckpt, float *cost_dev, float *grad_dev, void *stream)
 {
     if (!ctx) return ATP_ERR_INVALID;
     int ns = 0;
@@ -742,12 +743,96 @@ extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *co
     p.n_sub = ns;
     p.ckpt = ckpt;
     p.h = pp.h;
+    p.objective = objective;
     p.cost = cost_dev;
     p.grad = grad_dev;
     p.ckpt_buf = (float *)base;
     p.seg_buf = (float *)(base + ck_bytes);
     cudaError_t e = atp::launch_grad(p, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "grad launch");
+    return ATP_OK;
+}
+
+}  // namespace
+
+extern "C" int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                        const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
+                        const float *ctrl_dev, int K, int H, float dt, int n_sub, int ckpt,
+                        float *cost_dev, float *grad_dev, void *stream)
+{
+    return grad_impl(ctx, atp::kGradCost, veh, cost, terrain, x0, x0_dev, ctrl_dev, K, H, dt, n_sub, ckpt,
+                     cost_dev, grad_dev, stream);
+}
+
+extern "C" int atp_grad_margin(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
+                               const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
+                               const float *ctrl_dev, int K, int H, float dt, int n_sub, int ckpt,
+                               float *margin_dev, float *grad_dev, void *stream)
+{
+    return grad_impl(ctx, atp::kGradMargin, veh, cost, terrain, x0, x0_dev, ctrl_dev, K, H, dt, n_sub, ckpt,
+                     margin_dev, grad_dev, stream);
+}
+
+namespace {
+
+bool al8(const void *p) { return (uintptr_t)p % 8 == 0; }
+
+int refine_checks(atp_ctx *ctx, int K, int H)
+{
+    if (K < 1 || H < 1) return fail(ctx, ATP_ERR_INVALID, "need K >= 1 and H >= 1");
+    return ATP_OK;
+}
+
+}  // namespace
+
+extern "C" int atp_refine_init(atp_ctx *ctx, const float *grad_dev, int K, int H, float step, float *eta_dev,
+                               void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int rc = refine_checks(ctx, K, H);
+    if (rc != ATP_OK) return rc;
+    if (!grad_dev || !eta_dev || !al8(grad_dev)) return fail(ctx, ATP_ERR_INVALID, "grad_dev (8-byte aligned) and eta_dev are required");
+    if (!(step > 0.f) || !std::isfinite(step)) return fail(ctx, ATP_ERR_INVALID, "step must be finite and > 0");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    cudaError_t e = atp::launch_refine_init(grad_dev, K, H, step, eta_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine launch");
+    return ATP_OK;
+}
+
+extern "C" int atp_refine_trial(atp_ctx *ctx, const float *ctrl_dev, const float *grad_dev, const float *eta_dev,
+                                int K, int H, float rate_max, float *trial_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int rc = refine_checks(ctx, K, H);
+    if (rc != ATP_OK) return rc;
+    if (!ctrl_dev || !grad_dev || !eta_dev || !trial_dev || !al8(ctrl_dev) || !al8(grad_dev) || !al8(trial_dev))
+        return fail(ctx, ATP_ERR_INVALID, "a buffer is NULL or a [H][K][2] buffer not 8-byte aligned");
+    if (!(rate_max >= 0.f) || !std::isfinite(rate_max))
+        return fail(ctx, ATP_ERR_INVALID, "rate_max must be finite and >= 0");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    cudaError_t e = atp::launch_refine_trial(ctrl_dev, grad_dev, eta_dev, K, H, rate_max, trial_dev,
+                                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine launch");
+    return ATP_OK;
+}
+
+extern "C" int atp_refine_accept(atp_ctx *ctx, int K, int H, const float *trial_dev, const float *trial_cost_dev,
+                                 const float *trial_grad_dev, float *ctrl_dev, float *cost_dev, float *grad_dev,
+                                 float *eta_dev, void *stream)
+{
+    if (!ctx) return ATP_ERR_INVALID;
+    int rc = refine_checks(ctx, K, H);
+    if (rc != ATP_OK) return rc;
+    if (!trial_dev || !trial_cost_dev || !trial_grad_dev || !ctrl_dev || !cost_dev || !grad_dev || !eta_dev ||
+        !al8(trial_dev) || !al8(trial_grad_dev) || !al8(ctrl_dev) || !al8(grad_dev))
+        return fail(ctx, ATP_ERR_INVALID, "a buffer is NULL or a [H][K][2] buffer not 8-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    cudaError_t e = atp::launch_refine_accept(K, H, trial_dev, trial_cost_dev, trial_grad_dev, ctrl_dev, cost_dev,
+                                              grad_dev, eta_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refine launch");
     return ATP_OK;
 }
 
@@ -831,7 +916,8 @@ extern "C" int atp_plan_noalloc(const atp_vehicle *veh, const atp_cost *cost,
                            n_sub, &ns);
     if (rc != ATP_OK) return rc;
     if (!out_dev) return ATP_ERR_INVALID;
-    const ScratchLayout L = layout((size_t)N, (size_t)H);
+    const bool steps = best_margin_dev != nullptr;
+    const RegionLayout L = layout((size_t)N, (size_t)H, steps);
     if (L.total > kNoallocScratchBytes) return ATP_ERR_UNSUPPORTED;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return ATP_ERR_CUDA;
@@ -855,7 +941,8 @@ extern "C" int atp_plan_noalloc(const atp_vehicle *veh, const atp_cost *cost,
     p.margin = cand_margin_dev ? cand_margin_dev : (float *)(base + L.margin);
     p.flags = cand_flags_dev ? cand_flags_dev : (uint8_t *)(base + L.flags);
     p.xf = cand_xf_dev;
-    p.step_margin = (float *)(base + L.step_margin);
+    p.min_step = (int *)(base + L.min_step);
+    p.step_margin = steps ? (float *)(base + L.step_margin) : nullptr;
     p.out = out_dev;
     p.best_ctrl = best_ctrl_dev;
     p.best_margin = best_margin_dev;

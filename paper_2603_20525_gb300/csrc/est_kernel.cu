@@ -69,6 +69,8 @@ __device__ __forceinline__ void est_one(const PlanParams &p, int j, float &J, fl
     const float h = p.h;
     const bool cm = T.has_cm != 0;
     double J64 = 0.0;
+    float msm = CUDART_INF_F;      // smallest per-step margin so far and its control step
+    int mstep = 0;
     // each interval's control is loaded one interval ahead, so the load's
     // latency overlaps the Euler steps
     float2 un = p.H > 0 ? __ldg(p.ctrl + j) : make_float2(0.f, 0.f);
@@ -158,6 +160,10 @@ __device__ __forceinline__ void est_one(const PlanParams &p, int j, float &J, fl
             acc2(vx, vxl, h * ax);
         }
         if (p.step_margin) p.step_margin[(size_t)k * p.N + j] = sm;
+        if (sm < msm) {
+            msm = sm;
+            mstep = k;
+        }
     }
     // final state: goal test and terminal cost Phi (Sec. IV-C)
     {
@@ -180,6 +186,7 @@ __device__ __forceinline__ void est_one(const PlanParams &p, int j, float &J, fl
     if (p.cost) p.cost[j] = J;
     if (p.margin) p.margin[j] = margin;
     if (p.flags) p.flags[j] = fl;
+    if (p.min_step) p.min_step[j] = mstep;
     if (p.xf) {
 #pragma unroll
         for (int c = 0; c < 7; ++c) p.xf[(size_t)c * p.N + j] = xs[c];

@@ -32,7 +32,9 @@ struct PlanParams {
     float *margin;            // [N] or nullptr
     uint8_t *flags;           // [N] or nullptr
     float *xf;                // [13][N] or nullptr
-    float *step_margin;       // [H][N] or nullptr
+    float *step_margin;       // [H][N] or nullptr: each control step's minimum U_ESM
+    int *min_step;            // [N] or nullptr: control step of each candidate's smallest
+                              // per-step margin (the final state folded into step H-1)
     int tex_format;           // TEX_F32 or TEX_BF16
     int acc64;                // accumulate the running cost in FP64
     int lanes;                // 0: by batch size; else 1, 2 or 4 lanes per candidate

@@ -64,10 +64,9 @@ __device__ __forceinline__ void plan_tail(const PlanParams &p, int j, bool leade
     __syncthreads();
     if (!s_last) return;
 
-    // ---- last CTA: result, best controls and per-step margins, reset scratch
+    // ---- last CTA: result, best controls (and per-step margins), reset scratch
     __shared__ unsigned long long s_best;
     __shared__ unsigned int s_nf;
-    __shared__ unsigned long long s_mkey[kPlanBlock];
     if (threadIdx.x == 0) {
         s_best = atomicAdd(&p.scratch->key, 0ull);
         s_nf = atomicAdd(&p.scratch->count, 0u);
@@ -75,28 +74,21 @@ __device__ __forceinline__ void plan_tail(const PlanParams &p, int j, bool leade
     __syncthreads();
     const uint32_t best = (uint32_t)(s_best & 0x7fffffffull);
     const size_t N = (size_t)p.N;
-    unsigned long long mk = ~0ull;
     for (int k = threadIdx.x; k < p.H; k += blockDim.x) {
-        const float2 u = __ldcg(p.ctrl + (size_t)k * N + best);
         if (p.best_ctrl) {
+            const float2 u = __ldcg(p.ctrl + (size_t)k * N + best);
             p.best_ctrl[2 * k] = clamp_keep_nan(u.x, -p.V.ddmax, p.V.ddmax);
             p.best_ctrl[2 * k + 1] = u.y;
         }
-        const float m = __ldcg(p.step_margin + (size_t)k * N + best);
-        if (p.best_margin) p.best_margin[k] = m;
-        const unsigned long long c = ((unsigned long long)order_u32(m) << 32) | (unsigned int)k;
-        mk = c < mk ? c : mk;
+        if (p.best_margin && p.step_margin) p.best_margin[k] = __ldcg(p.step_margin + (size_t)k * N + best);
     }
-    s_mkey[threadIdx.x] = mk;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int t = 1; t < blockDim.x; ++t) mk = s_mkey[t] < mk ? s_mkey[t] : mk;
         atp_plan_out o;
         o.best_idx = best;
         o.n_feasible = s_nf;
         o.best_cost = __ldcg(p.cost + best);
         o.best_min_margin = __ldcg(p.margin + best);
-        o.best_min_step = (int32_t)(mk & 0xffffffffull);
+        o.best_min_step = p.min_step ? __ldcg(p.min_step + best) : 0;
         o.reserved = 0;
         *p.out = o;
         // restore the scratch for the next plan on this stream

@@ -5,7 +5,9 @@
 // A candidate's state lives in registers for the whole horizon (in one
 // thread, or repeated in the two or four threads that share its wheels), so a
 // rollout step reads memory only for the four bilinear terrain lookups (16
-// texels).
+// texels).  A wheel is written as its geometry (what depends on position and
+// attitude: the lookup, the slope normal, the extension) and its forces
+// (what depends on the velocities).
 //
 // Precision.  The arithmetic is FP32, compiled without implicit FMA
 // contraction: every fused multiply-add is written as fmaf (or as fma2, its
@@ -13,8 +15,9 @@
 // of each expression is fixed by the source and the same in every kernel that
 // inlines it.  The slowly varying, large-magnitude
 // state components (position, heading and linear velocity) are accumulated as
-// unevaluated sums hi + lo of two floats (Dekker's Fast2Sum per step, Knuth's
-// TwoSum where the start is taken into the terrain frame), and positions are
+// unevaluated sums hi + lo of two floats (Kahan's compensated summation per
+// step, Knuth's TwoSum where the start is taken into the terrain frame), and
+// positions are
 // kept relative to the terrain origin and split into an integer cell and a
 // fraction before the lookup.  Without that, the rounding of a 20-100 m
 // coordinate (1e-6 m per Euler step) walks the wheels across the terrain by
@@ -77,17 +80,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// hi + lo += d: Dekker's Fast2Sum, exact while |hi| >= |d|, which holds for
-// a state component and its increment over one Euler step except near the
-// component's zero, where the plain FP32 sum it then reduces to is accurate
-// to the component's own small magnitude.  Three operations instead of
-// TwoSum's six.
+// hi + lo += d, with the carried low part folded into the increment first
+// (Kahan's compensated summation; the new low part by Dekker's Fast2Sum,
+// exact while |hi| >= |d + lo|, which holds for a state component and its
+// increment over one Euler step except near the component's zero, where
+// the plain FP32 sum it reduces to is accurate to the component's own small
+// magnitude).  Folding keeps hi the FP32 value nearest the compensated sum,
+// so the dynamics, which read hi alone, see the state as exactly
+// accumulated; a low part summed on its own instead leaves hi the plain FP32
+// running sum, whose error grows with every step (a constant increment
+// rounds the same way each time).
 __device__ __forceinline__ void acc2(float &hi, float &lo, float d)
 {
-    const float s = __fadd_rn(hi, d);
-    const float e = __fsub_rn(d, __fsub_rn(s, hi));
+    const float y = __fadd_rn(d, lo);
+    const float s = __fadd_rn(hi, y);
+    lo = __fsub_rn(y, __fsub_rn(s, hi));
     hi = s;
-    lo = __fadd_rn(lo, e);
 }
 
 // Energy stability margin (Sec. IV-B): U = +/- M g Rbar (1 - sin(|phi| +
@@ -207,10 +215,91 @@ __device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a
     }
 }
 
+// What the force of one wheel needs from the state's position and attitude
+// alone: the local slope-normal tau in B (and 1 / tau_z) and the suspension
+// extension chi at the contact point, and the costmap there.
+struct WheelGeo {
+    float tx, ty, tz, itz, chi, cost;
+};
+
+// One wheel's geometry (Sec. IV-A): contact point P = p + R rho, the terrain
+// below it, the slope-normal tau ~ (-f_x, -f_y, 1) (reading Q1) resolved in
+// B and the extension chi along it.  (icx, fcx), (icy, fcy) is the CoM's cell
+// and fraction, z_hi + z_lo its height.  PAIRED takes the lookup's two axes
+// as packed pairs: the same bits, measured faster with two lanes per
+// candidate and slower with one or four.
+template <int TEX, bool PAIRED = false>
+__device__ __forceinline__ WheelGeo wheel_geo(const Veh &V, const Terrain &T, const float R[9], int icx,
+                                              int icy, float fcx, float fcy, float z_hi, float z_lo,
+                                              float rx, float ry, bool &off)
+{
+    // offset of the contact point from the CoM in W: R (rx, ry, -(h+R))
+    const float2 oxy = fma2(splat2(rx), make_float2(R[0], R[3]),
+                            fma2(splat2(ry), make_float2(R[1], R[4]),
+                                 make_float2(-V.hR * R[2], -V.hR * R[5])));
+    const float oz = fmaf(rx, R[6], fmaf(ry, R[7], -V.hR * R[8]));
+    // terrain below the contact point
+    float a, bb;
+    int i, j;
+    if constexpr (PAIRED) {
+        axis_xy(icx, icy, make_float2(fcx, fcy), oxy, T.inv_cell, T.nx, T.ny, i, j, a, bb, off);
+    } else {
+        i = axis(icx, fcx, oxy.x, T.inv_cell, T.nx, a, off);
+        j = axis(icy, fcy, oxy.y, T.inv_cell, T.ny, bb, off);
+    }
+    const float4 t = bilerp<TEX>(T, i, j, a, bb);
+    // tau in B = R^T (-f_x, -f_y, 1)
+    const float2 txy = fma2(make_float2(-R[3], -R[4]), splat2(t.z),
+                            fma2(make_float2(-R[0], -R[1]), splat2(t.y), make_float2(R[6], R[7])));
+    WheelGeo g;
+    g.tx = txy.x;
+    g.ty = txy.y;
+    g.tz = fmaf(-R[5], t.z, fmaf(-R[2], t.y, R[8]));
+    g.itz = rcp(g.tz);
+    // P_z - f with the compensated CoM height
+    g.chi = ((z_hi - t.x) + (oz + z_lo)) * g.itz;
+    g.cost = t.w;
+    return g;
+}
+
 // What one wheel contributes to the force and moment sums.
 struct WheelOut {
     float Fz, Fy, cost;
 };
+
+// One wheel's forces (Sec. IV-A) at the body velocity (vx, vy, vz) and rate
+// (wx, wy, wz): the contact point's body velocity v + w x rho, the extension
+// rate chi_dot, spring and damper with liftoff, slip angle and sigmoid tire
+// force.  PAIRED takes the extension rate's inner pair as a packed pair (the
+// same bits).
+template <bool PAIRED = false>
+__device__ __forceinline__ WheelOut wheel_dyn(const Veh &V, const WheelGeo &g, float vx, float vy, float vz,
+                                              float wx, float wy, float wz, float rx, float ry, float k,
+                                              float b, float Fs, float di)
+{
+    // body velocity of the contact point: v + w x rho
+    const float vix = fmaf(-wz, ry, fmaf(-wy, V.hR, vx));
+    const float viy = fmaf(wx, V.hR, fmaf(wz, rx, vy));
+    const float viz = fmaf(-wy, rx, fmaf(wx, ry, vz));
+    // omega x b_z in B is (w_y, -w_x, 0)
+    float chid;
+    if constexpr (PAIRED) {
+        const float2 rel = fma2(splat2(g.chi), make_float2(wx, -wy), make_float2(viy, vix));
+        chid = fmaf(g.tz, viz, fmaf(g.ty, rel.x, g.tx * rel.y)) * g.itz;
+    } else {
+        chid = fmaf(g.tz, viz, fmaf(g.ty, fmaf(g.chi, wx, viy), g.tx * fmaf(-g.chi, wy, vix))) * g.itz;
+    }
+    const float Fk = fmaxf(fmaf(-k, g.chi, Fs), 0.f);
+    const float Fz = Fk > 0.f ? fmaxf(fmaf(-b, chid, Fk), 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
+    const float alpha = atan2_r(viy, vix) - di;
+    const float Ca = V.C * alpha;
+    const float Fy = Fz * (-Ca * V.mu) * rsq(fmaf(Ca, Ca, V.mu2));
+    WheelOut w;
+    w.Fz = Fz;
+    w.Fy = Fy;
+    w.cost = g.cost;
+    return w;
+}
 
 // Per-step body quantities the four wheels share.
 struct Body {
@@ -221,63 +310,15 @@ struct Body {
     float vx, vy, vz, wx, wy, wz;
 };
 
-// One wheel (Sec. IV-A): contact point P = p + R rho, its body velocity
-// v + w x rho, terrain below it, extension chi and rate against the local
-// slope-normal tau ~ (-f_x, -f_y, 1) (reading Q1), spring and damper with
-// liftoff, slip angle and sigmoid tire force.  PAIRED takes the lookup's two
-// axes and the suspension rate's inner pair as packed pairs: the same bits,
-// measured faster with two lanes per candidate and slower with one or four.
+// One wheel (Sec. IV-A): its geometry, then its forces at the body's
+// velocities.
 template <int TEX, bool PAIRED = false>
-__device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const Body &B,
-                                          float rx, float ry, float k, float b, float Fs,
-                                          float di, bool &off)
+__device__ __forceinline__ WheelOut wheel(const Veh &V, const Terrain &T, const Body &B, float rx, float ry,
+                                          float k, float b, float Fs, float di, bool &off)
 {
-    const float *R = B.R;
-    // offset of the contact point from the CoM in W: R (rx, ry, -(h+R))
-    const float2 oxy = fma2(splat2(rx), make_float2(R[0], R[3]),
-                            fma2(splat2(ry), make_float2(R[1], R[4]),
-                                 make_float2(-V.hR * R[2], -V.hR * R[5])));
-    const float oz = fmaf(rx, R[6], fmaf(ry, R[7], -V.hR * R[8]));
-    // body velocity of the contact point: v + w x rho
-    const float vix = fmaf(-B.wz, ry, fmaf(-B.wy, V.hR, B.vx));
-    const float viy = fmaf(B.wx, V.hR, fmaf(B.wz, rx, B.vy));
-    const float viz = fmaf(-B.wy, rx, fmaf(B.wx, ry, B.vz));
-    // terrain below the contact point
-    float a, bb;
-    int i, j;
-    if constexpr (PAIRED) {
-        axis_xy(B.icx, B.icy, make_float2(B.fcx, B.fcy), oxy, T.inv_cell, T.nx, T.ny, i, j, a, bb, off);
-    } else {
-        i = axis(B.icx, B.fcx, oxy.x, T.inv_cell, T.nx, a, off);
-        j = axis(B.icy, B.fcy, oxy.y, T.inv_cell, T.ny, bb, off);
-    }
-    const float4 t = bilerp<TEX>(T, i, j, a, bb);
-    // tau in B = R^T (-f_x, -f_y, 1)
-    const float2 txy = fma2(make_float2(-R[3], -R[4]), splat2(t.z),
-                            fma2(make_float2(-R[0], -R[1]), splat2(t.y), make_float2(R[6], R[7])));
-    const float tx = txy.x, ty = txy.y;
-    const float tz = fmaf(-R[5], t.z, fmaf(-R[2], t.y, R[8]));
-    const float itz = rcp(tz);
-    // P_z - f with the compensated CoM height
-    const float chi = ((B.z_hi - t.x) + (oz + B.z_lo)) * itz;
-    // omega x b_z in B is (w_y, -w_x, 0)
-    float chid;
-    if constexpr (PAIRED) {
-        const float2 rel = fma2(splat2(chi), make_float2(B.wx, -B.wy), make_float2(viy, vix));
-        chid = fmaf(tz, viz, fmaf(ty, rel.x, tx * rel.y)) * itz;
-    } else {
-        chid = fmaf(tz, viz, fmaf(ty, fmaf(chi, B.wx, viy), tx * fmaf(-chi, B.wy, vix))) * itz;
-    }
-    const float Fk = fmaxf(fmaf(-k, chi, Fs), 0.f);
-    const float Fz = Fk > 0.f ? fmaxf(fmaf(-b, chid, Fk), 0.f) : 0.f;   // = F_k + max(-b chid, -F_k)
-    const float alpha = atan2_r(viy, vix) - di;
-    const float Ca = V.C * alpha;
-    const float Fy = Fz * (-Ca * V.mu) * rsq(fmaf(Ca, Ca, V.mu2));
-    WheelOut w;
-    w.Fz = Fz;
-    w.Fy = Fy;
-    w.cost = t.w;
-    return w;
+    const WheelGeo g = wheel_geo<TEX, PAIRED>(V, T, B.R, B.icx, B.icy, B.fcx, B.fcy, B.z_hi, B.z_lo, rx, ry,
+                                              off);
+    return wheel_dyn<PAIRED>(V, g, B.vx, B.vy, B.vz, B.wx, B.wy, B.wz, rx, ry, k, b, Fs, di);
 }
 
 }  // namespace atp

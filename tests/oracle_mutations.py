@@ -105,6 +105,9 @@ SAMPLER = [
  ("sin for both", "sigma_rate * r * cos(2.0 * M_PI * u2)", "sigma_rate * r * sin(2.0 * M_PI * u2)"),
  ("sigmas swapped", "o[0] = nom[0] + sigma_rate", "o[0] = nom[0] + sigma_acc"),
  ("nominal at candidate 1", "if (j == 0) {", "if (j == 1) {"),
+ ("one call per step", "(uint64_t)(k / 4)", "(uint64_t)k"),
+ ("word pairs swapped", "u1 = unif23((s & 1) ? w[2] : w[0], low);", "u1 = unif23((s & 1) ? w[0] : w[2], low);"),
+ ("low uniform from other bits", "(w >> 9) & 0x7FFFFFull", "(w >> 8) & 0x7FFFFFull"),
 ]
 
 ADJOINT = [
@@ -128,6 +131,21 @@ BF16 = [
  ("plane slopes not removed", "w_gx = bf16_round((g.gx.astype(np.float32) - px).astype(np.float32))",
   "w_gx = bf16_round(g.gx.astype(np.float32))"),
  ("y slope from x", "py = (P[..., 2] * inv).astype(np.float32)", "py = (P[..., 1] * inv).astype(np.float32)"),
+]
+
+MODEL = [
+ ("R[4] sign", "R[4] = cph * cps + sph * sps * sth;", "R[4] = cph * cps - sph * sps * sth;"),
+ ("chi from the wrong corner", "T chi = T(P[2] - ter[0]) / tauB[2];", "T chi = T(P[2] - ter[1]) / tauB[2];"),
+ ("minimum step last on ties", "if (value(sm) < value(best_sm)) {", "if (value(sm) <= value(best_sm)) {"),
+ ("position not accumulated exactly", "constexpr bool kSrbWide[13] = {true,", "constexpr bool kSrbWide[13] = {false,"),
+ ("planar aBx sign", "T aBx = zeta[1] - wz * vy;", "T aBx = zeta[1] + wz * vy;"),
+ ("planar margin without gravity", "margin = k.abar - Tfabs(aBy - gB[1]);", "margin = k.abar - Tfabs(aBy);"),
+]
+
+COUNT = [
+ ("multiplications not counted", "inline Cnt operator*(const Cnt &a, const Cnt &b) { ++g_cnt.mul; ",
+  "inline Cnt operator*(const Cnt &a, const Cnt &b) { "),
+ ("divisions counted twice", "{ ++g_cnt.div; return Cnt(a.v / b.v); }", "{ g_cnt.div += 2; return Cnt(a.v / b.v); }"),
 ]
 
 EQUIVALENT = {("srb.c", "Fx on front"), ("terrain_tools.c", "ray direction")}
@@ -165,6 +183,8 @@ if __name__ == "__main__":
               run("terrain_tools.c", TERRAIN, "test_oracle_terrain_tools.py") +
               run("sampler.c", SAMPLER, "test_oracle_sampler.py") +
               run("adjoint.cpp", ADJOINT, "test_oracle_adjoint.py") +
+              run("model.hpp", MODEL, "test_oracle_templated.py") +
+              run("emul32.cpp", COUNT, "test_bench_host.py") +
               run("__init__.py", BF16, "test_oracle_bf16.py"))
     print("missed:", missed or "none beyond the two equivalent changes")
     sys.exit(1 if missed else 0)

@@ -41,17 +41,18 @@ def gpu_est(ctx, w, costmap=None):
     return r
 
 
-def check_est(g, w, costmap=None, tail_frac=None):
+def check_est(g, w, costmap=None):
     ter = oracle.Terrain(w.terrain.heights, w.terrain.cell, w.terrain.x0, w.terrain.y0, costmap=costmap)
     o = oracle.est_plan(w.vehicle, w.cost, ter, w.x0, w.ctrl, w.dt, w.n_sub)
-    sens = parity.conditioning(oracle, w.vehicle, w.cost, ter, w.x0, w.ctrl, w.dt, w.n_sub, o, model="est")
-    v = parity.classify(g, o, sens, w.vehicle, model="est")
+    cond = parity.conditioning(oracle, w.vehicle, w.cost, ter, w.x0, w.ctrl, w.dt, w.n_sub, o, model="est")
+    v = parity.classify(g, o, cond, w.vehicle, model="est")
     print("parity", w.name, v["stats"])
     bad = np.nonzero(v["fail"])[0]
     assert bad.size == 0, [(int(j), float(v["err"][j]), float(v["bound"][j])) for j in bad[:5]]
-    cap = v["stats"]["cap"] if tail_frac is None else max(3, int(tail_frac * v["stats"]["feasible"]))
-    assert v["stats"]["tail"] <= cap, v["stats"]
-    assert v["stats"]["switch_misses"] <= v["stats"]["cap"], v["stats"]
+    assert v["stats"]["tail"] <= v["stats"]["cap"], v["stats"]
+    if v["stats"]["feasible"] >= 200:
+        parity.assert_fp32_level(v["stats"])
+    assert v["stats"]["switch_misses"] <= v["stats"]["switch_cap"], v["stats"]
     ck = v["checked"]
     assert np.array_equal(g["flags"][ck], o["flags"][ck])
     assert np.array_equal(g["flags"][~v["near"]] & 1, o["flags"][~v["near"]] & 1)
@@ -79,8 +80,7 @@ def check_est(g, w, costmap=None, tail_frac=None):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_est_plain_parity(ctx, seed):
     w = gen.workload_est(seed)
-    v = check_est(gpu_est(ctx, w), w)
-    assert v["stats"]["strict_frac"] >= 0.6
+    check_est(gpu_est(ctx, w), w)
 
 
 def test_est_scaled_parity_per_candidate_start(ctx):
@@ -92,11 +92,7 @@ def test_est_with_costmap_and_high_traction(ctx):
     """Obstacles and a path boundary through the costmap at the wheels, and a
     tire with mu > abar / g so that the lateral-acceleration constraint can
     bind (with mu = 0.6 it cannot on level ground).  mu = 1.8 puts the turns
-    just past the bound.  In these saturated turns up to 5 % of the feasible
-    candidates land between one and four times the conditioning bound (none
-    beyond), against 2 % elsewhere: every one of them is within the factor-4
-    tail, but the tail is wider than the protocol's default cap, so this
-    test states its own."""
+    just past the bound; the protocol is the same as everywhere else."""
     w = gen.workload_est(2, N=2048, H=40)
     w.vehicle = dict(w.vehicle, mu=1.8)
     # constant steering rates from -1 to 1 rad/s: the sharper turns exceed abar
@@ -108,7 +104,7 @@ def test_est_with_costmap_and_high_traction(ctx):
                            w.terrain.x0, w.terrain.y0)
     cm = cm.astype(np.float32)
     g = gpu_est(ctx, w, costmap=cm)
-    check_est(g, w, costmap=cm, tail_frac=0.05)
+    check_est(g, w, costmap=cm)
     assert np.count_nonzero((g["flags"] & 1) == 0) > 10        # the constraint binds
     assert np.count_nonzero(g["cost"] > 1e5) > 10               # obstacles are hit
 
@@ -155,8 +151,8 @@ def test_est_bf16_terrain_against_decoded_oracle(ctx):
     h_dec, gx, gy, _, _ = oracle.bf16_terrain(t.heights, t.cell)
     od = oracle.Terrain(h_dec, t.cell, t.x0, t.y0, gx=gx, gy=gy)
     ref = oracle.est_plan(w.vehicle, w.cost, od, w.x0, w.ctrl, w.dt, w.n_sub)
-    sens = parity.conditioning(oracle, w.vehicle, w.cost, od, w.x0, w.ctrl, w.dt, w.n_sub, ref, model="est")
-    v = parity.classify(g, ref, sens, w.vehicle, model="est")
+    cond = parity.conditioning(oracle, w.vehicle, w.cost, od, w.x0, w.ctrl, w.dt, w.n_sub, ref, model="est")
+    v = parity.classify(g, ref, cond, w.vehicle, model="est")
     print("est bf16 vs decoded oracle", v["stats"])
     assert v["stats"]["fails"] == 0 and v["stats"]["tail"] <= v["stats"]["cap"]
     assert g["best_idx"] == lexmin(g["cost"], g["flags"])

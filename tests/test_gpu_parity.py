@@ -63,21 +63,25 @@ def check_candidates(g, o, w, ctrl=None, x0=None):
     ctrl = w.ctrl if ctrl is None else ctrl
     x0 = w.x0 if x0 is None else x0
     ter = oracle.Terrain.of(w.terrain)
-    sens = parity.conditioning(oracle, w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, o)
-    v = parity.classify(g, o, sens, w.vehicle)
+    cond = parity.conditioning(oracle, w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, o)
+    v = parity.classify(g, o, cond, w.vehicle)
     print("parity", w.name, v["stats"])
-    # every feasible candidate agrees within max(1e-4, KAPPA x its own FP64
-    # conditioning), except a capped few that took the other side of a switch
+    # every feasible candidate agrees within max(1e-4, KAPPA x the FP32
+    # reference's own error), except a capped few that took the other side of
+    # a switch
     bad = np.nonzero(v["fail"])[0]
     assert bad.size == 0, [(int(j), float(v["err"][j]), float(v["bound"][j])) for j in bad[:5]]
     assert v["stats"]["tail"] <= v["stats"]["cap"], v["stats"]
-    assert v["stats"]["switch_misses"] <= v["stats"]["cap"], v["stats"]
+    assert v["stats"]["switch_misses"] <= v["stats"]["switch_cap"], v["stats"]
     # all flag bits agree on the candidates that held the bound; the
     # feasibility bit agrees on every candidate away from a switch
     ck = v["checked"]
     assert np.array_equal(g["flags"][ck], o["flags"][ck])
     sure = ~v["near"]
     assert np.array_equal(g["flags"][sure] & 1, o["flags"][sure] & 1)
+    # over the workload, as accurate as FP32 arithmetic itself
+    if v["stats"]["feasible"] >= 200:
+        parity.assert_fp32_level(v["stats"])
     return v
 
 
@@ -128,8 +132,7 @@ def test_plain_plan_parity(ctx):
     w = gen.workload_plain(0)
     g = gpu_plan(ctx, w)
     o = oracle_plan(w)
-    s = check_plan(g, o, w)
-    assert s["strict_frac"] >= 0.6
+    check_plan(g, o, w)
 
 
 @pytest.mark.parametrize("seed", [1, 2])
@@ -143,8 +146,7 @@ def test_scaled_plan_parity(ctx):
     w = gen.workload_scaled(0)
     g = gpu_plan(ctx, w)
     o = oracle_plan(w)
-    s = check_plan(g, o, w)
-    assert s["strict_frac"] >= 0.5
+    check_plan(g, o, w)
 
 
 @pytest.mark.parametrize("lanes", [1, 2, 4])
@@ -190,15 +192,15 @@ def test_paper_configuration_sampled(ctx):
     """The real-time configuration of Sec. IV-D at full size: 204,288
     candidates of 16 steps of 0.25 s (800 Euler steps of 5 ms), steering
     only, one thread per candidate.  The reduction is checked bit-exactly
-    over all GPU outputs; every output of 3000 sampled candidates, the chosen
-    one among them, against the oracle."""
+    over all GPU outputs; every output of 12000 sampled candidates, the
+    chosen one among them, against the oracle."""
     w = gen.workload_paper(0)
     g = gpu_plan(ctx, w)
     assert g["best_idx"] == lexmin(g["cost"], g["flags"])
     assert g["n_feasible"] == int(np.count_nonzero(g["flags"] & 1))
     assert g["best_cost"] == g["cost"][g["best_idx"]]
     rng = np.random.default_rng(1)
-    idx = np.unique(np.concatenate([rng.choice(w.N, 3000, replace=False), [g["best_idx"]]]))
+    idx = np.unique(np.concatenate([rng.choice(w.N, 12000, replace=False), [g["best_idx"]]]))
     ws = gen.Workload(w.name + "-sample", w.terrain, w.vehicle, w.cost, w.x0,
                       np.ascontiguousarray(w.ctrl[:, idx]), w.dt, w.n_sub)
     gs = {k: g[k][idx] for k in ("cost", "margin", "flags", "xf")}
@@ -273,9 +275,9 @@ def test_all_infeasible_and_ties(ctx):
     check_plan(g, o, ww, x0=x0, ctrl=ctrl)
     # nothing is feasible: the free fall is smooth, so every candidate's state
     # and cost still agree within the bound
-    sens = parity.conditioning(oracle, ww.vehicle, ww.cost, oracle.Terrain.of(ww.terrain), x0, ctrl,
+    cond = parity.conditioning(oracle, ww.vehicle, ww.cost, oracle.Terrain.of(ww.terrain), x0, ctrl,
                                ww.dt, ww.n_sub, o)
-    v = parity.classify(g, o, sens, ww.vehicle)
+    v = parity.classify(g, o, cond, ww.vehicle)
     assert np.all(v["ok"])
     assert g["best_idx"] not in range(40, 48)
 

@@ -117,3 +117,55 @@ def test_gradient_with_the_esm_soft_term_active(slope_deg):
                 smooth += 1
                 assert G[k, j, comp] == pytest.approx(a, rel=2e-4, abs=2e-4), (j, k, comp)
     assert smooth >= 0.7 * checked
+
+
+def fd_margin(w, t, j, k, c, step):
+    u = w.ctrl[:, j, :].astype(np.float64)
+    up, dn = u.copy(), u.copy()
+    up[k, c] += step
+    dn[k, c] -= step
+    x0 = (w.x0[j] if w.x0.ndim == 2 else w.x0).astype(np.float64)
+    return (oracle.margin_f64(w.vehicle, w.cost, t, x0, up, w.dt, w.n_sub) -
+            oracle.margin_f64(w.vehicle, w.cost, t, x0, dn, w.dt, w.n_sub)) / (2 * step)
+
+
+@pytest.mark.parametrize("slope_deg", [0.0, 20.0, -20.0])
+def test_margin_gradient_against_central_differences(slope_deg):
+    """The ESM margin (min U_ESM over the trajectory, Sec. IV-B) and its tape
+    gradient: the margin equals the oracle's, the gradient matches FP64
+    central differences wherever the margin is smooth at that scale (the
+    state holding the minimum does not change under the step), and it is
+    exactly zero for every control applied after that state (causality)."""
+    import math
+    v = gen.vehicle_baseline()
+    c = gen.cost_default(1000.0, 0.0)
+    n, cell = 256, 0.5
+    ys = np.arange(n) * cell - 64.0
+    xs = np.arange(n) * cell - 10.0
+    hts = (math.tan(math.radians(slope_deg)) * ys[:, None] + 0.3 * np.sin(xs[None, :] / 1.7)
+           + 0.2 * np.cos(ys[:, None] / 2.3)).astype(np.float32)
+    ter = gen.Terrain(hts, cell, -10.0, -64.0)
+    t = oracle.Terrain(hts, cell, -10.0, -64.0)
+    x0 = gen.settled_state(ter, v, 0.0, 0.0, 0.0, 7.0)
+    H, dt, n_sub = 20, 0.05, 5
+    rng = np.random.default_rng(3)
+    ctrl = np.stack([rng.normal(0, 0.4, (H, 4)), rng.normal(0, 0.3, (H, 4))], -1).astype(np.float32)
+    w = gen.Workload("margin", ter, v, c, x0, ctrl, dt, n_sub)
+    M, G = oracle.grad_margin(v, c, t, x0, ctrl, dt, n_sub)
+    r = oracle.rollout(v, c, t, x0, ctrl, dt, n_sub, want_step_margin=True)
+    assert np.array_equal(M, r["margin"])
+    smooth = checked = 0
+    for j in range(4):
+        kmin = int(np.argmin(r["step_margin"][:, j]))
+        # controls after the minimum's control step cannot move it
+        assert np.all(G[kmin + 1:, j, :] == 0.0)
+        for k in range(0, kmin + 1, max(1, (kmin + 1) // 5)):
+            for comp in (0, 1):
+                a, b = fd_margin(w, t, j, k, comp, 1e-6), fd_margin(w, t, j, k, comp, 1e-5)
+                checked += 1
+                if abs(a - b) > 1e-3 * max(abs(a), 1e-1):
+                    continue
+                smooth += 1
+                assert G[k, j, comp] == pytest.approx(a, rel=2e-4, abs=2e-3), (j, k, comp)
+    assert smooth >= 0.6 * checked
+    assert np.abs(G).max() > 1.0          # the margin does depend on the controls

@@ -43,3 +43,28 @@ def test_warm_start_shift_rule():
     want = [prev[min(k + 1, 4)] for k in range(8)]
     for j in range(3):
         assert np.array_equal(s[:, j, :], np.array(want, dtype=np.float64))
+
+
+def test_draws_follow_the_documented_word_and_bit_map():
+    """Each draw from numpy's independent Philox4x64-10 by the documented map:
+    one call at counter (j, k // 4, nonce, 0) serves four steps, words (w0, w1)
+    for k % 4 in {0, 2} and (w2, w3) for {1, 3}, bits 63..41 of each for
+    k % 4 < 2 and bits 31..9 for k % 4 >= 2, then the Box-Muller pair."""
+    key, nonce, N, H = (np.uint64(0x1234567), np.uint64(0x89ABCDEF)), 5, 7, 9
+    s = oracle.sample(None, 0, 0.2, 0.3, (int(key[0]), int(key[1])), nonce, N, H)
+    for j in range(1, N):
+        for k in range(H):
+            ctr = np.array([j, k // 4, nonce, 0], dtype=np.uint64)
+            # numpy's Philox advances its counter by one before each block
+            prev = ctr.copy()
+            prev[0] -= np.uint64(1)
+            w = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=prev).random_raw(4)
+            a, b = (w[2], w[3]) if k % 2 else (w[0], w[1])
+            if k % 4 >= 2:
+                ua, ub = (int(a) >> 9) & 0x7FFFFF, (int(b) >> 9) & 0x7FFFFF
+            else:
+                ua, ub = int(a) >> 41, int(b) >> 41
+            u1, u2 = (ua + 0.5) / 8388608.0, (ub + 0.5) / 8388608.0
+            r = np.sqrt(-2.0 * np.log(u1))
+            np.testing.assert_allclose(s[k, j], [0.2 * r * np.cos(2 * np.pi * u2), 0.3 * r * np.sin(2 * np.pi * u2)],
+                                       rtol=1e-13, atol=1e-15)

@@ -31,6 +31,10 @@ def variants():
     yield "offmap", gen.Workload(w.name, w.terrain, w.vehicle, w.cost, x0, w.ctrl, w.dt, w.n_sub)
     s = gen.workload_scaled(0, N=2048, H=60)
     yield "scaled", s
+    # the goal circle around the start: every candidate is frozen at its first
+    # state, so every control step ties for the smallest margin (the first wins)
+    yield "frozen", gen.Workload(w.name, w.terrain, w.vehicle, dict(w.cost, goal_x=5.0, goal_y=25.6),
+                                 w.x0, w.ctrl, w.dt, w.n_sub)
 
 
 @pytest.mark.parametrize("name,w", list(variants()))
@@ -42,6 +46,8 @@ def test_templated_model_in_fp64_is_the_oracle(name, w):
         assert same_bits(r[k], q[k]), (name, k)
     # the control step of the smallest per-step margin (first on ties)
     assert np.array_equal(q["min_step"], np.argmin(r["step_margin"], axis=0))
+    if name == "frozen":
+        assert np.all(r["step_margin"] == r["step_margin"][0]) and np.all(q["min_step"] == 0)
 
 
 def test_templated_planar_model_matches_the_planar_oracle():
