@@ -125,13 +125,17 @@ __device__ __forceinline__ void cell_split(float hi, float lo, float inv_cell, i
 // (queries clamped to the map, reading Q10).
 // Written with selects rather than branches: the four wheels' lookups then
 // form one basic block that the compiler can interleave (measured on the
-// GB300: 9 % off a full-GPU plan, 3 to 10 % off the smaller ones).
+// GB300: 9 % off a full-GPU plan, 3 to 10 % off the smaller ones).  The cell
+// comes from one rounding-down conversion, which saturates for a huge or
+// infinite offset and gives 0 for NaN; the sum with the CoM cell wraps
+// (unsigned) instead of overflowing, and every out-of-range index is clamped
+// below, so no lookup leaves the map.
 __device__ __forceinline__ int axis(int ic, float fc, float o, float inv_cell, int n, float &a, bool &off)
 {
     const float u = fmaf(o, inv_cell, fc);
-    const float fl = floorf(u);
-    const int i = ic + (int)fmaxf(fminf(fl, 4194304.f), -4194304.f);
-    const float w = u - fl;
+    const int fi = __float2int_rd(u);
+    const int i = (int)((unsigned)ic + (unsigned)fi);
+    const float w = u - (float)fi;
     const bool below = i < 0, above = i >= n - 1;
     off = off || below || (above && (i > n - 1 || w > 0.f));
     a = below ? 0.f : (above ? 1.f : w);
@@ -144,10 +148,10 @@ __device__ __forceinline__ void axis_xy(int icx, int icy, float2 fc, float2 o, f
                                         int ny, int &i, int &j, float &a, float &b, bool &off)
 {
     const float2 u = fma2(o, splat2(inv_cell), fc);
-    const float2 fl = make_float2(floorf(u.x), floorf(u.y));
-    const float2 w = sub2(u, fl);
-    const int ix = icx + (int)fmaxf(fminf(fl.x, 4194304.f), -4194304.f);
-    const int iy = icy + (int)fmaxf(fminf(fl.y, 4194304.f), -4194304.f);
+    const int fx = __float2int_rd(u.x), fy = __float2int_rd(u.y);
+    const float2 w = sub2(u, make_float2((float)fx, (float)fy));
+    const int ix = (int)((unsigned)icx + (unsigned)fx);
+    const int iy = (int)((unsigned)icy + (unsigned)fy);
     const bool bx = ix < 0, ex = ix >= nx - 1, by = iy < 0, ey = iy >= ny - 1;
     off = off || bx || (ex && (ix > nx - 1 || w.x > 0.f)) || by || (ey && (iy > ny - 1 || w.y > 0.f));
     a = bx ? 0.f : (ex ? 1.f : w.x);
