@@ -312,8 +312,26 @@ def run_paper_config(ctx, dev, stream, flush, peak, steps=10, warmup=3):
         b.record(stream)
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # terrain staging (a window of the texels in each CTA's shared memory),
+    # A/B against the plain kernel on the same plan: same result, its time.
+    # A 2 x 2 window stages nothing useful: it is the staged kernel's
+    # 512-thread CTAs alone.
+    from paper_2603_20525_gb300 import atp
+    ref = outs["out"].clone()
+    staged = []
+    for side in (2, 64, 120):
+        ctx.set_option(atp.OPT_STAGE_TERRAIN, side)
+        try:
+            ms_s = _time(lambda: ctx.plan(w.vehicle, w.cost, ter, x0, ctrl, w.dt, w.n_sub, out=outs),
+                         steps, warmup, stream, flush)
+        finally:
+            ctx.set_option(atp.OPT_STAGE_TERRAIN, 0)
+        staged.append({"window_nodes": f"{side} x {side}", "shared_kb": side * side * 16 / 1024,
+                       "ms_per_plan": ms_s, "vs_plain": ms_s / ms,
+                       "same_result": bool(torch.equal(outs["out"], ref))})
     return {"workload": f"{w.N} candidates x 16 steps of 0.25 s ({w.n_sub} Euler steps of 5 ms "
                         f"each), steering only, {w.terrain.nx}^2 heightmap at {w.terrain.cell} m",
+            "terrain_staging": staged,
             "ms_per_plan": ms, "planner_hz": 1000.0 / ms, "samples_per_s": w.N / (ms / 1000),
             "substeps_per_s": w.N * w.H * w.n_sub / (ms / 1000),
             "fp32_tflops": FLOPS_PER_SUBSTEP["paper"] * w.N * w.H * w.n_sub / (ms / 1000) / 1e12,

@@ -75,8 +75,10 @@ enum {
 /* context options (atp_set_option) */
 enum {
     ATP_OPT_COST_FP64 = 1,    /* accumulate the running cost in FP64 (default 0: FP32) */
-    ATP_OPT_LANES = 2         /* threads per candidate in atp_plan / atp_rollout: 0 chooses
+    ATP_OPT_LANES = 2,        /* threads per candidate in atp_plan / atp_rollout: 0 chooses
                                  by batch size (default), 1, 2 or 4 forces it */
+    ATP_OPT_STAGE_TERRAIN = 3 /* side in nodes (2..120) of a texel window staged in shared
+                                 memory by atp_plan / atp_rollout; 0 (default) off */
 };
 
 /* per-candidate flag bits */
@@ -173,8 +175,18 @@ size_t atp_terrain_bytes(int nx, int ny, int format);
  * in FP64 instead of FP32; ATP_OPT_LANES (0, 1, 2 or 4) sets the threads per
  * candidate of atp_plan and atp_rollout (two split the axles and four the
  * wheels: lower latency for small batches; one: more throughput once a batch
- * fills the GPU).  One and two lanes give the same bits; four sum the wheel
- * forces in another order, so their results differ in the last bits.
+ * fills the GPU).  One, two and four lanes give the same bits: every layout
+ * forms the axle sums and the force and moment totals in one order.
+ * ATP_OPT_STAGE_TERRAIN (0, or a side W from 2 to 120 nodes) stages a window
+ * of the texels in shared memory (Sec. IV-D's cached terrain lookups): each
+ * CTA of 512 threads first copies min(W, nx) x min(W, ny) texels (16 B each,
+ * at most 225 KB), centred a quarter of its side ahead of the start along
+ * the start heading and moved inside the map, then reads every lookup whose
+ * four corners lie in it from shared memory and the rest from global
+ * memory.  It applies to plans of one lane per candidate on F32X4 terrains
+ * from a shared start state (x0 on the host); other plans, atp_plan_batch
+ * and atp_plan_noalloc run unstaged.  The results are the same bits as the
+ * unstaged one-lane kernel's.
  * Returns ATP_ERR_INVALID for an unknown option or value. */
 int atp_set_option(atp_ctx *ctx, int option, int value);
 
@@ -256,10 +268,10 @@ typedef struct {
 /* Continuous batching: n_req (1..64) independent plans, each with its own
  * vehicle, terrain, candidates, horizon and outputs, in one kernel launch.
  * Each plan's results are bit-identical to a single atp_plan of the same
- * request on a context with the same ATP_OPT_LANES, alone or in any mix: a
- * plan runs four lanes where atp_plan would, and otherwise one or two, which
- * give the same bits (two only while the batch's threads stay within what a
- * two-lane plan alone may use, or when ATP_OPT_LANES forces two).  The
+ * request, alone or in any mix: a plan runs four lanes where atp_plan would,
+ * and otherwise one or two (two only while the batch's threads stay within
+ * what a two-lane plan alone may use, or when ATP_OPT_LANES forces two), and
+ * every layout gives the same bits.  The
  * context's scratch grows to the sum of the plans' needs; atp_reserve(ctx,
  * sum of N, max H) pre-sizes it for any batch within those totals.
  * Validation failures name the offending request in atp_last_error. */

@@ -22,6 +22,7 @@ ERRORS = {-1: "ATP_ERR_INVALID", -2: "ATP_ERR_UNSUPPORTED", -3: "ATP_ERR_NOMEM",
 F32X4, BF16X4 = 0, 1
 OPT_COST_FP64 = 1
 OPT_LANES = 2
+OPT_STAGE_TERRAIN = 3
 FEASIBLE, DONE, OFFMAP, NONFINITE = 1, 2, 4, 8
 TERRAIN_HAS_COSTMAP = 1
 

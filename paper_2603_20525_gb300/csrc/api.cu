@@ -22,6 +22,7 @@ struct atp_ctx {
     int device;
     int acc64;                // ATP_OPT_COST_FP64
     int lanes;                // ATP_OPT_LANES
+    int stage;                // ATP_OPT_STAGE_TERRAIN: window side in nodes, 0 off
     char err[256];
     void *scratch;            // reduction headers + per-plan candidate buffers
     size_t scratch_bytes;
@@ -291,6 +292,28 @@ void fill_problem(atp::PlanParams &p, const atp_state *x0, const float *x0_dev, 
     p.h = (float)((double)dt / (double)n_sub);
 }
 
+// The plan's kernel: staged (ATP_OPT_STAGE_TERRAIN) where the option
+// applies, i.e. a one-lane plan on F32 texels from a shared start state,
+// else the plain kernel.  The window of side min(stage, map side) nodes is
+// centred a quarter of its side ahead of the start along the heading, and
+// moved inside the map.
+cudaError_t launch_plan_for(const atp_ctx *ctx, atp::PlanParams &p, const atp_terrain &t, bool reduce,
+                            cudaStream_t stream)
+{
+    if (ctx->stage == 0 || p.tex_format != atp::TEX_F32 || p.x0_soa || atp::plan_lanes(p.lanes, p.N) != 1)
+        return atp::launch_plan(p, reduce, stream);
+    const int ww = std::min(ctx->stage, t.nx), wh = std::min(ctx->stage, t.ny);
+    const double cx = ((double)p.x0[0] - t.x0) / t.cell, cy = ((double)p.x0[1] - t.y0) / t.cell;
+    const double psi = p.x0[3];
+    const double ox = cx + 0.25 * ww * std::cos(psi) - 0.5 * ww, oy = cy + 0.25 * wh * std::sin(psi) - 0.5 * wh;
+    p.T.wx0 = (int)std::lround(std::min(std::max(ox, 0.0), (double)(t.nx - ww)));
+    p.T.wy0 = (int)std::lround(std::min(std::max(oy, 0.0), (double)(t.ny - wh)));
+    p.T.ww = ww;
+    p.T.wh = wh;
+    p.tex_format = atp::TEX_F32W;
+    return atp::launch_plan_staged(p, reduce, stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -308,6 +331,7 @@ int atp_create(atp_ctx **out, int device)
     ctx->device = device;
     ctx->acc64 = 0;
     ctx->lanes = 0;
+    ctx->stage = 0;
     ctx->err[0] = 0;
     ctx->batch = new (std::nothrow) atp::BatchParams;
     if (!ctx->batch) {
@@ -381,6 +405,12 @@ int atp_set_option(atp_ctx *ctx, int option, int value)
         if (value != 0 && value != 1 && value != 2 && value != 4)
             return fail(ctx, ATP_ERR_INVALID, "ATP_OPT_LANES takes 0, 1, 2 or 4");
         ctx->lanes = value;
+        return ATP_OK;
+    }
+    if (option == ATP_OPT_STAGE_TERRAIN) {
+        if (value != 0 && (value < 2 || value > atp::kStageMaxSide))
+            return fail(ctx, ATP_ERR_INVALID, "ATP_OPT_STAGE_TERRAIN takes 0 or 2..%d", atp::kStageMaxSide);
+        ctx->stage = value;
         return ATP_OK;
     }
     return fail(ctx, ATP_ERR_INVALID, "unknown option %d", option);
@@ -458,7 +488,7 @@ int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const a
     p.scratch = (atp::Scratch *)ctx->scratch;
     p.acc64 = ctx->acc64;
     p.lanes = ctx->lanes;
-    cudaError_t e = atp::launch_plan(p, true, (cudaStream_t)stream);
+    cudaError_t e = launch_plan_for(ctx, p, *terrain, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
     return ATP_OK;
 }
@@ -486,7 +516,7 @@ int atp_rollout(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, cons
     p.step_margin = step_margin_dev;
     p.acc64 = ctx->acc64;
     p.lanes = ctx->lanes;
-    cudaError_t e = atp::launch_plan(p, false, (cudaStream_t)stream);
+    cudaError_t e = launch_plan_for(ctx, p, *terrain, false, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "rollout launch");
     return ATP_OK;
 }
@@ -520,8 +550,8 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
         if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
         need += region_layout((size_t)q.N, (size_t)q.H, q.best_margin_dev != nullptr).total;
-        // four lanes sum in another order, so a plan keeps its own layout's
-        // four; two lanes give one lane's bits and are decided below
+        // a plan keeps the four lanes a single plan of its size runs; two
+        // are decided below (every layout gives the same bits)
         lanes[r] = atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1;
         threads += (long long)q.N * lanes[r];
     }

@@ -60,6 +60,13 @@ inline int plan_lanes(int forced, int N)
 }
 cudaError_t launch_plan(const PlanParams &p, bool reduce, cudaStream_t stream);
 
+// Terrain staging (one lane per candidate, F32 texels, a shared start
+// state): CTAs of kStageBlock threads, each of which first copies the window
+// p.T.(wx0, wy0, ww, wh) of the texel array into its shared memory.
+constexpr int kStageBlock = 512;
+constexpr int kStageMaxSide = 120;     // 120 x 120 texels = 225 KB
+cudaError_t launch_plan_staged(const PlanParams &p, bool reduce, cudaStream_t stream);
+
 // A ragged batch of plans in one launch.  The descriptors travel in the
 // kernel's parameter block (at most 32 KB), so a batch needs no device copy.
 constexpr int kMaxBatch = 64;

@@ -25,11 +25,13 @@ __device__ __forceinline__ float clamp_keep_nan(float v, float lo, float hi)
 // Empirical argmin of one plan (Sec. IV-D, reading Q7): the lexicographic
 // minimum of (infeasible, J, j) over the plan's n_ctas CTAs, then the last of
 // them writes the result.
+// BLOCK is the launch's threads per CTA.
+template <int BLOCK = kPlanBlock>
 __device__ __forceinline__ void plan_tail(const PlanParams &p, int j, bool leader, float J,
                                           bool feasible, unsigned n_ctas)
 {
-    __shared__ unsigned long long s_key[kPlanBlock / 32];
-    __shared__ unsigned int s_cnt[kPlanBlock / 32];
+    __shared__ unsigned long long s_key[BLOCK / 32];
+    __shared__ unsigned int s_cnt[BLOCK / 32];
     __shared__ bool s_last;
     unsigned long long key = ~0ull;
     if (leader)
@@ -51,7 +53,7 @@ __device__ __forceinline__ void plan_tail(const PlanParams &p, int j, bool leade
     if (threadIdx.x == 0) {
         unsigned long long bk = s_key[0];
         unsigned int bc = s_cnt[0];
-        for (int w = 1; w < kPlanBlock / 32; ++w) {
+        for (int w = 1; w < BLOCK / 32; ++w) {
             bk = s_key[w] < bk ? s_key[w] : bk;
             bc += s_cnt[w];
         }

@@ -58,8 +58,14 @@ struct Cost {
 
 // Texel formats (ATP_TERRAIN_*): F32 = float4 (f, f_x, f_y, cost) per node;
 // BF16 = four bf16 per node (f - plane, f_x - plane_x, f_y - plane_y, cost)
-// with the FP32 plane (c0, cx, cy) of the node's 8 x 8 block.
-enum { TEX_F32 = 0, TEX_BF16 = 1 };
+// with the FP32 plane (c0, cx, cy) of the node's 8 x 8 block.  F32W is F32
+// with a window of the texels staged in the CTA's shared memory (`atp_win`,
+// ww x wh nodes from node (wx0, wy0)): a lookup whose four corners lie in
+// the window reads them there, any other from global memory.
+enum { TEX_F32 = 0, TEX_BF16 = 1, TEX_F32W = 2 };
+
+// the staged window of TEX_F32W (dynamic shared memory of the staging kernel)
+extern __shared__ float4 atp_win[];
 
 struct Terrain {
     const float4 *tex;               // F32 texels, row-major
@@ -70,6 +76,7 @@ struct Terrain {
     int has_cm;                      // the texels carry a costmap
     float inv_cell;                  // 1 / cell
     float x0_hi, x0_lo, y0_hi, y0_lo;  // terrain origin
+    int wx0, wy0, ww, wh;            // TEX_F32W: the staged window (ww, wh >= 2)
 };
 
 // x + y = s + e exactly (Knuth's TwoSum; no ordering precondition).
@@ -213,6 +220,14 @@ __device__ __forceinline__ float4 bilerp(const Terrain &T, int i, int j, float a
     if (TEX == TEX_F32) {
         const float4 *r0 = T.tex + (size_t)j * T.nx + i;
         return lerp4(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + T.nx), __ldg(r0 + T.nx + 1), a, b, cm);
+    } else if (TEX == TEX_F32W) {
+        // one generic pointer into the window or the texel array, so that a
+        // warp whose lookups fall on both sides still issues four loads
+        const unsigned li = (unsigned)(i - T.wx0), lj = (unsigned)(j - T.wy0);
+        const bool in = li < (unsigned)(T.ww - 1) && lj < (unsigned)(T.wh - 1);
+        const float4 *r0 = in ? atp_win + (lj * (unsigned)T.ww + li) : T.tex + (size_t)j * T.nx + i;
+        const int s = in ? T.ww : T.nx;
+        return lerp4(r0[0], r0[1], r0[s], r0[s + 1], a, b, cm);
     } else {
         return lerp4(texel16(T, i, j), texel16(T, i + 1, j), texel16(T, i, j + 1),
                      texel16(T, i + 1, j + 1), a, b, cm);

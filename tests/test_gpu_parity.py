@@ -165,27 +165,36 @@ def test_lanes_option_parity(ctx, lanes):
         ctx.set_option(atp.OPT_LANES, 3)
 
 
-@pytest.mark.parametrize("goal_dx", [None, 8.0])
-def test_one_and_two_lanes_same_bits(ctx, goal_dx):
-    """A pair of lanes sums each axle and then the two axles, the order one
-    lane uses, so the two layouts agree bit for bit.  With the goal 8 m ahead
-    of the start, over half of the candidates reach it mid-horizon, where two
-    lanes compute the step and discard it and one lane skips it."""
+@pytest.mark.parametrize("case", ["plain", "goal", "costmap"])
+def test_every_lane_layout_same_bits(ctx, case):
+    """A pair of lanes sums each axle and then the two axles, and a quad
+    each axle by one shuffle and then the two axles by another, both in the
+    order one lane uses, so the three layouts agree bit for bit.  With the
+    goal 8 m ahead of the start, over half of the candidates reach it
+    mid-horizon, where two lanes compute the step and discard it and one and
+    four lanes skip it; with a costmap the lanes also sum the wheels' cost."""
     from paper_2603_20525_gb300 import atp
     w = gen.workload_scaled(3, N=3000, H=30)
-    if goal_dx is not None:
-        w = gen.Workload(w.name, w.terrain, w.vehicle, dict(w.cost, goal_x=10.0 + goal_dx), w.x0,
+    if case == "goal":
+        w = gen.Workload(w.name, w.terrain, w.vehicle, dict(w.cost, goal_x=18.0), w.x0,
                          w.ctrl, w.dt, w.n_sub)
+    terrain = None
+    if case == "costmap":
+        t = w.terrain
+        xs, ys = t.grid()
+        cm = (0.5 + 0.5 * np.sin(0.7 * xs) * np.cos(0.4 * ys)).astype(np.float32)
+        terrain = gen.Terrain(t.heights, t.cell, t.x0, t.y0, costmap=cm, name="costmap")
     outs = []
-    for lanes in (1, 2):
+    for lanes in (1, 2, 4):
         ctx.set_option(atp.OPT_LANES, lanes)
-        outs.append(gpu_plan(ctx, w))
+        outs.append(gpu_plan(ctx, w, terrain=terrain))
     ctx.set_option(atp.OPT_LANES, 0)
-    if goal_dx is not None:
+    if case == "goal":
         assert np.count_nonzero(outs[0]["flags"] & 2) > 1000      # ATP_FLAG_DONE
-    for k in ("cost", "margin", "flags", "xf", "best_ctrl", "best_margin"):
-        assert np.array_equal(outs[0][k], outs[1][k]), k
-    assert outs[0]["best_idx"] == outs[1]["best_idx"]
+    for o in outs[1:]:
+        for k in ("cost", "margin", "flags", "xf", "best_ctrl", "best_margin"):
+            assert outs[0][k].tobytes() == o[k].tobytes(), k
+        assert outs[0]["best_idx"] == o["best_idx"]
 
 
 def test_paper_configuration_sampled(ctx):
