@@ -40,6 +40,24 @@ def test_sincos_against_cuda_and_fp64():
     assert es <= 2.5 * es_ref and ec <= 2.5 * ec_ref
 
 
+def test_sincos_special_arguments():
+    """NaN comes out NaN from the library's reduction, infinities and
+    arguments from 2^17 up are CUDA's sincosf bit for bit, and the largest
+    argument the reduction takes still meets its bound."""
+    big = np.array([131072.0, -131072.0, 1e6, -3.5e7, 3e38, np.inf, -np.inf], np.float32)
+    edge = np.array([np.nextafter(np.float32(131072.0), np.float32(0)), -100000.0], np.float32)
+    a = np.concatenate([[np.nan, -np.nan], big, edge]).astype(np.float32)
+    o = run(a, np.ones_like(a))
+    assert np.all(np.isnan(o[:2, :2]))
+    nb = 2 + len(big)
+    assert np.array_equal(o[2:nb, 0], o[2:nb, 2], equal_nan=True)
+    assert np.array_equal(o[2:nb, 1], o[2:nb, 3], equal_nan=True)
+    assert np.all(np.isnan(o[nb - 2:nb, :2]))
+    x = a[nb:].astype(np.float64)
+    assert np.abs(o[nb:, 0] - np.sin(x)).max() <= 2e-6
+    assert np.abs(o[nb:, 1] - np.cos(x)).max() <= 2e-6
+
+
 def test_atan2_against_cuda_and_fp64():
     rng = np.random.default_rng(1)
     n = 300000
