@@ -45,8 +45,8 @@ __device__ __forceinline__ float pair_sum(float v, unsigned mask)
 // (fl, fr, rl, rr) and forms the axle sums, then the totals, in that order
 // too, so all three layouts give the same bits.  The body-level arithmetic is repeated bit-identically on
 // every lane of a candidate, so lanes never exchange state, only the five
-// force/moment sums and the costmap sum, and with four lanes the step's four
-// sincos, one per lane.  ACC selects the running cost's
+// force/moment sums and the costmap sum, and the step's four sincos, which
+// the lanes split between them.  ACC selects the running cost's
 // accumulator: kAccF32, kAccF64, or kAccRuntime (p.acc64 decides; the batch
 // kernel, which would otherwise inline twice as many variants).  A
 // compile-time choice keeps the step loop free of the uniform branch.
@@ -125,10 +125,11 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     continue;
                 }
                 // four lanes split the step's four sincos (psi, theta, phi,
-                // delta; one each) and exchange them by shuffle, the same
-                // bits as computing all four (measured 8 % off a
-                // 16384-candidate plan with four lanes)
-                float sps, cps, sth, cth, sph, cph, cd4 = 1.f;
+                // delta; one each) and two lanes split them two and two,
+                // exchanging them by shuffle: the same bits as computing all
+                // four (measured 8 % off a 16384-candidate plan with four
+                // lanes, 2.4 % with two)
+                float sps, cps, sth, cth, sph, cph, cdl = 1.f;
                 if constexpr (LANES == 4) {
                     float s1, c1;
                     sincos_r(q == 0 ? psi : q == 1 ? th : q == 2 ? ph : d, s1, c1);
@@ -138,7 +139,21 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                     cth = __shfl_sync(qmask, c1, 1, 4);
                     sph = __shfl_sync(qmask, s1, 2, 4);
                     cph = __shfl_sync(qmask, c1, 2, 4);
-                    cd4 = __shfl_sync(qmask, c1, 3, 4);
+                    cdl = __shfl_sync(qmask, c1, 3, 4);
+                } else if constexpr (LANES == 2) {
+                    // lane 0: psi and phi; lane 1: theta and delta
+                    float s1, c1, s2, c2;
+                    sincos_r(q == 0 ? psi : th, s1, c1);
+                    sincos_r(q == 0 ? ph : d, s2, c2);
+                    const float os1 = __shfl_xor_sync(qmask, s1, 1), oc1 = __shfl_xor_sync(qmask, c1, 1);
+                    const float os2 = __shfl_xor_sync(qmask, s2, 1), oc2 = __shfl_xor_sync(qmask, c2, 1);
+                    sps = q == 0 ? s1 : os1;
+                    cps = q == 0 ? c1 : oc1;
+                    sth = q == 0 ? os1 : s1;
+                    cth = q == 0 ? oc1 : c1;
+                    sph = q == 0 ? s2 : os2;
+                    cph = q == 0 ? c2 : oc2;
+                    cdl = q == 0 ? oc2 : c2;
                 } else {
                     sincos_r(psi, sps, cps);
                     sincos_r(th, sth, cth);
@@ -191,8 +206,8 @@ __device__ __forceinline__ void rollout_one(const PlanParams &p, int j, int q, u
                 // gravity in B: R^T (0, 0, -g)
                 const float gBx = -V.g * R[6], gBy = -V.g * R[7], gBz = -V.g * R[8];
                 float cd;
-                if constexpr (LANES == 4) {
-                    cd = cd4;
+                if constexpr (LANES > 1) {
+                    cd = cdl;
                 } else {
                     float sd;
                     sincos_r(d, sd, cd);
