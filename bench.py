@@ -283,6 +283,21 @@ def cpu_baseline(w, budget_s=10.0):
             break
     out["single_thread"] = {"value": n1 * m * w.H / el1, "unit": "rollout-steps/s", "cores": 1,
                             "sample": f"{n1} plans of the first {m} candidates ({el1:.1f} s), FP64"}
+    # the plain configuration (1024 candidates x H = 40 x 10 Euler steps), whole plans
+    import gen
+    wp = gen.workload_plain(0)
+    tp = oracle.Terrain.of(wp.terrain)
+    n2, t0 = 0, time.perf_counter()
+    while True:
+        oracle.plan(wp.vehicle, wp.cost, tp, wp.x0, wp.ctrl, wp.dt, wp.n_sub)
+        n2 += 1
+        el2 = time.perf_counter() - t0
+        if el2 >= budget_s / 4 or n2 >= 2000:
+            break
+    out["plain"] = {"value": n2 * wp.N * wp.H / el2, "unit": "rollout-steps/s", "cores": omp_threads(),
+                    "ms_per_plan": 1e3 * el2 / n2,
+                    "sample": f"{n2} whole plans of the plain workload ({wp.N} x {wp.H} x {wp.n_sub}, "
+                              f"{el2:.1f} s), FP64"}
     return out
 
 
@@ -389,6 +404,20 @@ def run_variants(ctx, dev, stream, flush, steps=10):
                steps, 3, stream, flush)
     out["bf16_terrain_plan"] = {"workload": "the scaled plan on BF16 texels", "ms_per_plan": ms,
                                 "rollout_steps_per_s": ws.N * ws.H / (ms / 1e3)}
+    # the plain configuration (1024 candidates x H = 40 at dt = 0.05 s, 10 Euler steps)
+    wp = gen.workload_plain(0)
+    terp = ctx.terrain_prepare(torch.as_tensor(wp.terrain.heights).to(dev), wp.terrain.cell,
+                               wp.terrain.x0, wp.terrain.y0)
+    ctrlp = torch.as_tensor(wp.ctrl).to(dev)
+    x0p = [float(v) for v in wp.x0]
+    op = ctx.plan(wp.vehicle, wp.cost, terp, x0p, ctrlp, wp.dt, wp.n_sub, want_candidates=False,
+                  want_best_margin=False)
+    ms = _time(lambda: ctx.plan(wp.vehicle, wp.cost, terp, x0p, ctrlp, wp.dt, wp.n_sub, out=op),
+               steps, 3, stream, flush)
+    out["plain_plan"] = {"workload": f"plain: {wp.N} candidates x H={wp.H} at dt={wp.dt} s "
+                                     f"({wp.n_sub} Euler steps), 256^2 map at 0.2 m, "
+                                     f"{ctx.plan_lanes(wp.N)} threads per candidate",
+                         "ms_per_plan": ms, "rollout_steps_per_s": wp.N * wp.H / (ms / 1e3)}
     t = gen.terrain_tile(2048, 5, lod_sigma=0.0)
     h = torch.as_tensor(t.heights).to(dev)
     sm = torch.empty_like(h)
