@@ -165,16 +165,19 @@ def test_lanes_option_parity(ctx, lanes):
         ctx.set_option(atp.OPT_LANES, 3)
 
 
-@pytest.mark.parametrize("case", ["plain", "goal", "costmap"])
+@pytest.mark.parametrize("case", ["plain", "goal", "costmap", "tipping"])
 def test_every_lane_layout_same_bits(ctx, case):
     """A pair of lanes sums each axle and then the two axles, and a quad
     each axle by one shuffle and then the two axles by another, both in the
     order one lane uses, so the three layouts agree bit for bit.  With the
     goal 8 m ahead of the start, over half of the candidates reach it
     mid-horizon, where two lanes compute the step and discard it and one and
-    four lanes skip it; with a costmap the lanes also sum the wheels' cost."""
+    four lanes skip it; with a costmap the lanes also sum the wheels' cost.
+    The paper's configuration (3000 of its candidates) tips most of them
+    over: their states diverge to huge and non-finite values, which the
+    lanes' split sincos must treat exactly as one lane does."""
     from paper_2603_20525_gb300 import atp
-    w = gen.workload_scaled(3, N=3000, H=30)
+    w = gen.workload_paper(0, N=3000) if case == "tipping" else gen.workload_scaled(3, N=3000, H=30)
     if case == "goal":
         w = gen.Workload(w.name, w.terrain, w.vehicle, dict(w.cost, goal_x=18.0), w.x0,
                          w.ctrl, w.dt, w.n_sub)
@@ -191,6 +194,8 @@ def test_every_lane_layout_same_bits(ctx, case):
     ctx.set_option(atp.OPT_LANES, 0)
     if case == "goal":
         assert np.count_nonzero(outs[0]["flags"] & 2) > 1000      # ATP_FLAG_DONE
+    if case == "tipping":
+        assert np.count_nonzero(outs[0]["flags"] & 8) > 1000      # ATP_FLAG_NONFINITE
     for o in outs[1:]:
         for k in ("cost", "margin", "flags", "xf", "best_ctrl", "best_margin"):
             assert outs[0][k].tobytes() == o[k].tobytes(), k
