@@ -268,10 +268,12 @@ typedef struct {
 /* Continuous batching: n_req (1..64) independent plans, each with its own
  * vehicle, terrain, candidates, horizon and outputs, in one kernel launch.
  * Each plan's results are bit-identical to a single atp_plan of the same
- * request, alone or in any mix: a plan runs four lanes where atp_plan would,
- * and otherwise one or two (two only while the batch's threads stay within
- * what a two-lane plan alone may use, or when ATP_OPT_LANES forces two), and
- * every layout gives the same bits.  The
+ * request, alone or in any mix, since every layout gives the same bits.  The
+ * batch chooses each plan's threads per candidate for the batch as a whole:
+ * ATP_OPT_LANES if set; else one, raised in request order to the four (or
+ * two) lanes a plan of its size would run alone while the batch's threads
+ * stay within what a two-lane plan alone may use (2 x 28672), else to two if
+ * those fit.  The
  * context's scratch grows to the sum of the plans' needs; atp_reserve(ctx,
  * sum of N, max H) pre-sizes it for any batch within those totals.
  * Validation failures name the offending request in atp_last_error. */

@@ -550,20 +550,29 @@ extern "C" int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_
         if (!q.out_dev) return fail(ctx, ATP_ERR_INVALID, "request %d: out_dev is NULL", r);
         if (q.N > (1 << 29)) return fail(ctx, ATP_ERR_UNSUPPORTED, "request %d: N too large for a batch", r);
         need += region_layout((size_t)q.N, (size_t)q.H, q.best_margin_dev != nullptr).total;
-        // a plan keeps the four lanes a single plan of its size runs; two
-        // are decided below (every layout gives the same bits)
-        lanes[r] = atp::plan_lanes(ctx->lanes, q.N) == 4 ? 4 : 1;
+        lanes[r] = ctx->lanes ? ctx->lanes : 1;
         threads += (long long)q.N * lanes[r];
     }
-    // Two lanes pay only while the GPU is mostly empty: a plan that would run
-    // two lanes alone runs them in a batch while the batch's threads stay
-    // within what a two-lane plan alone may use (or when two are forced).
-    for (int r = 0; r < n_req; ++r) {
-        const long long N = reqs[r].N;
-        if (atp::plan_lanes(ctx->lanes, reqs[r].N) == 2 &&
-            (ctx->lanes == 2 || threads + N <= 2LL * atp::kLanes2MaxN)) {
-            lanes[r] = 2;
-            threads += N;
+    // Several lanes per candidate pay only while the GPU is mostly empty, and
+    // every layout gives the same bits, so the batch chooses each plan's
+    // lanes for the batch as a whole (unless ATP_OPT_LANES forces them):
+    // every plan starts at one lane, and in request order a plan that would
+    // run four (or two) lanes alone gets them while the batch's threads stay
+    // within what a two-lane plan alone may use, else two if those fit.
+    // Measured on the GB300 on the 32-vehicle serving mix: at 80 requests/s
+    // per vehicle p99 fell from 55 to 32 ms, unchanged at 20 to 40.
+    if (!ctx->lanes) {
+        const long long budget = 2LL * atp::kLanes2MaxN;
+        for (int r = 0; r < n_req; ++r) {
+            const long long N = reqs[r].N;
+            const int alone = atp::plan_lanes(0, reqs[r].N);
+            if (alone == 4 && threads + 3 * N <= budget) {
+                lanes[r] = 4;
+                threads += 3 * N;
+            } else if (alone >= 2 && threads + N <= budget) {
+                lanes[r] = 2;
+                threads += N;
+            }
         }
     }
     for (int r = 0; r < n_req; ++r)

@@ -121,7 +121,7 @@ def test_two_lane_plan_alone_and_in_a_full_batch_bitwise(ctx):
     """A plan that runs two lanes alone (20000 candidates) keeps two lanes in
     a batch that leaves the GPU mostly empty and runs one lane in a batch of
     three such plans (60000 threads at one lane each, past a two-lane plan's
-    own 57344); one and two lanes give the same bits, so it matches atp_plan
+    own 57344); every layout gives the same bits, so it matches atp_plan
     either way."""
     qs = prepare(ctx, requests_mix())
     big = next(q for q in qs if q["ctrl"].shape[1] == 20000)
@@ -138,6 +138,26 @@ def test_two_lane_plan_alone_and_in_a_full_batch_bitwise(ctx):
     torch.cuda.synchronize()
     for q in trio:
         same(q["out"], single)
+
+
+def test_four_lane_plan_demoted_in_a_full_batch_bitwise(ctx):
+    """A plan that runs four lanes alone (1000 candidates) keeps four in a
+    batch that leaves room for them (alone, or ahead of two 20000-candidate
+    plans, which then run one lane each) and runs one lane ahead of three of
+    them (61000 threads at one lane each, past a two-lane plan's own 57344).
+    Every layout gives the same bits, so it matches atp_plan in each."""
+    qs = prepare(ctx, requests_mix())
+    small = next(q for q in qs if q["ctrl"].shape[1] == 1000)
+    big = next(q for q in qs if q["ctrl"].shape[1] == 20000)
+    assert ctx.plan_lanes(1000) == 4
+    single = fresh_outputs(small)
+    ctx.plan(small["veh"], small["cost"], small["terrain"], small["x0"], small["ctrl"], small["dt"],
+             small["n_sub"], out=single)
+    for n_big in (0, 2, 3):
+        mix = [dict(small, out=fresh_outputs(small))] + [dict(big, out=fresh_outputs(big)) for _ in range(n_big)]
+        ctx.plan_batch(mix)
+        torch.cuda.synchronize()
+        same(mix[0]["out"], single)
 
 
 def test_batched_plan_parity_with_oracle(ctx):
