@@ -110,10 +110,11 @@ class DeviceArena:
 
 
 def request_layout(N: int, H: int):
-    """Byte offsets of one request's buffers inside its arena block."""
-    parts = [("ctrl", (H, N, 2), "f4"), ("cost", (N,), "f4"), ("margin", (N,), "f4"),
-             ("flags", (N,), "u1"), ("best_ctrl", (H, 2), "f4"), ("best_margin", (H,), "f4"),
-             ("out", (6,), "i4")]
+    """Byte offsets of one request's buffers inside its arena block: its
+    candidates' controls.  The plan writes its best controls straight into
+    the vehicle's warm-start buffer and its result into the stream's result
+    row; the per-candidate outputs stay in the library's scratch."""
+    parts = [("ctrl", (H, N, 2), "f4")]
     off, lay = 0, []
     for name, shape, dt in parts:
         n = int(np.prod(shape)) * np.dtype(dt).itemsize
@@ -221,6 +222,9 @@ class Server:
         self.arena = DeviceArena(arena_bytes, device=f"cuda:{device}")
         self.inflight = [None] * streams
         self.pinned = torch.empty((self.max_batch * streams, 6), dtype=torch.int32).pin_memory()
+        # each stream's result rows (atp_plan_out), read back by one copy per batch
+        self.outs = [torch.zeros((self.max_batch, 6), dtype=torch.int32, device=f"cuda:{device}")
+                     for _ in range(streams)]
         self.h_max = h_max
         # (seconds, trace time): the longest interval between two passes of
         # the serving loop (served) or the longest launch-to-result time
@@ -234,24 +238,23 @@ class Server:
         dts = {"f4": t.float32, "u1": t.uint8, "i4": t.int32}
         return {name: self.arena.view(off + o, shape, dts[dt]) for name, o, shape, dt in lay}
 
-    def _enqueue(self, ctx, stream, reqs, blocks):
-        """Sample every request's candidates, run the batch, keep the warm start."""
+    def _enqueue(self, ctx, stream, reqs, blocks, outs):
+        """Sample every request's candidates and run the batch.  Each plan
+        writes its best controls into its vehicle's warm-start buffer (after
+        its own sampler has read them, on the same stream) and its result
+        into row i of `outs`."""
         qs = []
-        for r, off in zip(reqs, blocks):
+        for i, (r, off) in enumerate(zip(reqs, blocks)):
             v = self.vehicles[r.vehicle]
-            b = self._buffers(off, r.N, r.H)
+            ctrl = self._buffers(off, r.N, r.H)["ctrl"]
             ctx.sample(r.N, r.H, self.sigma[0], self.sigma[1], v.key, r.rid,
                        prev=v.prev[:v.prev_H] if v.prev_H > 0 else None, shift=1,
-                       out=b["ctrl"], stream=stream)
-            qs.append(dict(veh=v.veh, cost=v.cost, terrain=v.terrain, x0=v.x0, ctrl=b["ctrl"],
-                           dt=r.dt, n_sub=0, out=dict(out=b["out"], best_ctrl=b["best_ctrl"],
-                                                     best_margin=b["best_margin"], cost=b["cost"],
-                                                     margin=b["margin"], flags=b["flags"])))
+                       out=ctrl, stream=stream)
+            qs.append(dict(veh=v.veh, cost=v.cost, terrain=v.terrain, x0=v.x0, ctrl=ctrl,
+                           dt=r.dt, n_sub=0, out=dict(out=outs[i], best_ctrl=v.prev[:r.H])))
         ctx.plan_batch(qs, stream=stream)
-        for r, q in zip(reqs, qs):
-            v = self.vehicles[r.vehicle]
-            v.prev[:r.H].copy_(q["out"]["best_ctrl"])
-            v.prev_H = r.H
+        for r in reqs:
+            self.vehicles[r.vehicle].prev_H = r.H
         return qs
 
     # -- continuous batching ----------------------------------------------
@@ -302,11 +305,10 @@ class Server:
                 stream = self.streams[s]
                 t_launch = time.perf_counter() - t0
                 with torch.cuda.stream(stream):
-                    qs = self._enqueue(self.ctxs[s], stream, batch, blocks)
+                    self._enqueue(self.ctxs[s], stream, batch, blocks, self.outs[s])
                     base = s * self.max_batch
                     host = self.pinned[base:base + len(batch)]
-                    for i, q in enumerate(qs):
-                        host[i].copy_(q["out"]["out"], non_blocking=True)
+                    host.copy_(self.outs[s][:len(batch)], non_blocking=True)
                     ev = torch.cuda.Event()
                     ev.record(stream)
                 for r in batch:
@@ -339,20 +341,18 @@ class Server:
                 time.sleep(2e-5)
             rec = Record(r.rid, r.vehicle, r.N, r.H, r.t_arrive)
             off = self.arena.alloc(request_layout(r.N, r.H)[1])
-            b = self._buffers(off, r.N, r.H)
+            ctrl = self._buffers(off, r.N, r.H)["ctrl"]
             v = self.vehicles[r.vehicle]
+            out_dev = self.outs[0][0]
             rec.t_launch = time.perf_counter() - t0
             with torch.cuda.stream(stream):
                 ctx.sample(r.N, r.H, self.sigma[0], self.sigma[1], v.key, r.rid,
                            prev=v.prev[:v.prev_H] if v.prev_H > 0 else None, shift=1,
-                           out=b["ctrl"], stream=stream)
-                ctx.plan(v.veh, v.cost, v.terrain, v.x0, b["ctrl"], r.dt, 0,
-                         out=dict(out=b["out"], best_ctrl=b["best_ctrl"], best_margin=b["best_margin"],
-                                  cost=b["cost"], margin=b["margin"], flags=b["flags"]),
-                         stream=stream)
-                v.prev[:r.H].copy_(b["best_ctrl"])
+                           out=ctrl, stream=stream)
+                ctx.plan(v.veh, v.cost, v.terrain, v.x0, ctrl, r.dt, 0,
+                         out=dict(out=out_dev, best_ctrl=v.prev[:r.H]), stream=stream)
                 v.prev_H = r.H
-                out_host[0].copy_(b["out"], non_blocking=True)
+                out_host[0].copy_(out_dev, non_blocking=True)
             stream.synchronize()
             rec.t_done = time.perf_counter() - t0
             if rec.t_done - rec.t_launch > self.max_loop_gap[0]:

