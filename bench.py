@@ -515,7 +515,7 @@ def main():
                     help="threads per candidate (ATP_OPT_LANES; 0 chooses by batch size)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="seconds of the 32-vehicle request stream (0: skip)")
-    ap.add_argument("--serve-rates", default="30,40,60,80",
+    ap.add_argument("--serve-rates", default="30,40,60,80,100",
                     help="per-vehicle request rates (Hz) of the serving sweep, comma-separated ('' skips)")
     ap.add_argument("--sweep-seconds", type=float, default=6.0, help="seconds of each sweep stream")
     args = ap.parse_args()
