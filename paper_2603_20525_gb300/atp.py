@@ -349,6 +349,29 @@ class Context:
         self._check(rc, "atp_plan_batch")
         return [q["out"] for q in requests]
 
+    # -- raw-pointer forms for a caller that keeps its own buffers and
+    # -- marshalled structs (the serving loop); the same C calls as above
+    def sample_raw(self, N, H, sigma_rate, sigma_acc, key, nonce, prev_ptr, prev_H, shift, out_ptr,
+                   stream_ptr):
+        """atp_sample with device pointers (ints) and a stream handle (int)."""
+        rc = self.lib.atp_sample(self.h, prev_ptr or None, int(prev_H), int(shift), float(sigma_rate),
+                                 float(sigma_acc), int(key[0]), int(key[1]), int(nonce), int(N), int(H),
+                                 out_ptr, stream_ptr)
+        self._check(rc, "atp_sample")
+
+    def plan_raw(self, veh_p, cost_p, ter_p, x0_p, ctrl_ptr, N, H, dt, n_sub, out_ptr, best_ctrl_ptr,
+                 stream_ptr):
+        """atp_plan with marshalled structs (ctypes pointers), device pointers
+        (ints) and a stream handle; no per-candidate outputs."""
+        rc = self.lib.atp_plan(self.h, veh_p, cost_p, ter_p, x0_p, None, ctrl_ptr, int(N), int(H),
+                               float(dt), int(n_sub), out_ptr, best_ctrl_ptr, None, None, None, None,
+                               None, stream_ptr)
+        self._check(rc, "atp_plan")
+
+    def plan_batch_raw(self, arr, n, stream_ptr):
+        """atp_plan_batch over a prepared PlanRequest array."""
+        self._check(self.lib.atp_plan_batch(self.h, arr, int(n), stream_ptr), "atp_plan_batch")
+
     def grad(self, veh: dict, cst: dict, terrain: Terrain, x0, ctrl, dt, n_sub=0, ckpt=10,
              stream=None, objective="cost"):
         """J [K] and dJ/dctrl [H, K, 2] of K candidates (atp_grad), or with
