@@ -205,7 +205,12 @@ def admit(queue, vehicles, max_batch: int, slot_candidates: int, alloc):
 
 
 class Server:
-    """Continuous batching over `streams` CUDA streams (one atp context each)."""
+    """Continuous batching over `streams` CUDA streams (one atp context each).
+    The vehicles' parameters (vehicle, cost, start state) are marshalled for
+    the C-ABI once, here: change a vehicle's parameters by building a new
+    Server.  Each plan writes its best controls into its vehicle's warm-start
+    buffer and its result into a per-stream result row; it keeps no per-step
+    margins."""
 
     def __init__(self, vehicles, streams: int = 2, slot_candidates: int = 1 << 17,
                  arena_bytes: int = 1 << 30, max_batch: int = 64, sigma=(0.2, 0.3),
