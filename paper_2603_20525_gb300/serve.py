@@ -204,6 +204,18 @@ def admit(queue, vehicles, max_batch: int, slot_candidates: int, alloc):
     return batch, blocks, keep
 
 
+def check_trace(trace, vehicles):
+    """Every request names a vehicle of the fleet and a horizon that fits its
+    warm-start buffer, into which the plan writes its best controls: refused
+    up front otherwise (ValueError), before anything is launched."""
+    for r in trace:
+        if not 0 <= r.vehicle < len(vehicles):
+            raise ValueError(f"request {r.rid}: no vehicle {r.vehicle}")
+        rows = int(vehicles[r.vehicle].prev.shape[0])
+        if not 1 <= r.H <= rows:
+            raise ValueError(f"request {r.rid}: H = {r.H} outside 1..{rows}")
+
+
 class Server:
     """Continuous batching over `streams` CUDA streams (one atp context each).
     The vehicles' parameters (vehicle, cost, start state) are marshalled for
@@ -275,6 +287,7 @@ class Server:
     # -- continuous batching ----------------------------------------------
     def serve(self, trace, idle_sleep: float = 2e-5):
         """Run the trace in real time; returns one Record per request."""
+        check_trace(trace, self.vehicles)
         with collector_paused():
             return self._serve(trace, idle_sleep)
 
@@ -342,6 +355,7 @@ class Server:
     # -- baseline ----------------------------------------------------------
     def sequential(self, trace):
         """The plain single-plan path: one request at a time, in arrival order."""
+        check_trace(trace, self.vehicles)
         with collector_paused():
             return self._sequential(trace)
 

@@ -151,3 +151,18 @@ def test_collector_paused_restores_state():
         assert not gc.isenabled()          # a caller's own pause is kept
     finally:
         gc.enable()
+
+
+def test_trace_check_refuses_horizons_beyond_the_warm_start():
+    """A plan writes its best controls into its vehicle's warm-start buffer,
+    so a horizon longer than that buffer, or an unknown vehicle, is refused
+    before anything runs."""
+    from types import SimpleNamespace
+    from paper_2603_20525_gb300 import serve
+    vehicles = [SimpleNamespace(prev=np.zeros((150, 2), np.float32)) for _ in range(2)]
+    ok = [serve.Request(0, 0, 1024, 150, 0.02, 0.0), serve.Request(1, 1, 1024, 1, 0.02, 0.0)]
+    serve.check_trace(ok, vehicles)
+    for bad in (serve.Request(2, 0, 1024, 151, 0.02, 0.0), serve.Request(3, 1, 1024, 0, 0.02, 0.0),
+                serve.Request(4, 2, 1024, 40, 0.02, 0.0)):
+        with pytest.raises(ValueError):
+            serve.check_trace(ok + [bad], vehicles)
