@@ -77,3 +77,38 @@ def test_served_plan_matches_oracle(fleet):
         ref = oracle.plan(f.vehicle, f.cost, oracle.Terrain.of(f.terrain), f.x0, ctrl_h, w.dt, w.n_sub)
         check_plan(g, ref, w)
     ctx.close()
+
+
+def test_largest_serving_request_sampled():
+    """The serving mix's largest request at full size: 32768 candidates of
+    150 steps at dt = 0.05 s (1500 Euler steps each) on a 2048^2 tile, drawn
+    on the device and run through the batch path.  The reduction is checked
+    bit-exactly over every output, and 1500 sampled candidates (the chosen one
+    among them) against the oracle."""
+    from paper_2603_20525_gb300 import atp
+    from tests.test_gpu_parity import check_candidates, lexmin
+    f = gen.fleet(1, seed=3, sides=(2048,))[0]
+    N, H, dt = 32768, 150, 0.05
+    ctx = atp.Context(0)
+    t = f.terrain
+    ter = ctx.terrain_prepare(torch.as_tensor(t.heights).cuda(), t.cell, t.x0, t.y0)
+    ctrl = ctx.sample(N, H, 0.2, 0.3, tuple(int(k) for k in f.key), 7)
+    q = dict(veh=f.vehicle, cost=f.cost, terrain=ter, x0=[float(v) for v in f.x0], ctrl=ctrl, dt=dt,
+             n_sub=0, out=atp.plan_outputs(N, H, xf=True))
+    ctx.plan_batch([q])
+    torch.cuda.synchronize()
+    o = q["out"]
+    g = {k: v.cpu().numpy() for k, v in o.items() if k != "out"}
+    g.update(atp.decode_out(o["out"]))
+    g["xf"] = g["xf"].T.copy()
+    assert g["best_idx"] == lexmin(g["cost"], g["flags"])
+    assert g["n_feasible"] == int(np.count_nonzero(g["flags"] & 1))
+    ctrl_h = ctrl.cpu().numpy()
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([rng.choice(N, 1500, replace=False), [g["best_idx"]]]))
+    ws = gen.Workload("serving-largest-sample", f.terrain, f.vehicle, f.cost, f.x0,
+                      np.ascontiguousarray(ctrl_h[:, idx]), dt, gen.n_substeps(dt))
+    gs = {k: g[k][idx] for k in ("cost", "margin", "flags", "xf")}
+    check_candidates(gs, oracle.plan(f.vehicle, f.cost, oracle.Terrain.of(f.terrain), f.x0,
+                                     ws.ctrl, dt, ws.n_sub), ws)
+    ctx.close()
