@@ -289,7 +289,12 @@ int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *
  *             zero for a steering rate beyond its limit (the clamp)
  *   ckpt      control steps between stored states (0 selects 10); the
  *             reverse pass recomputes one such segment at a time, so memory
- *             is (H / ckpt + ckpt n_sub) x 320 bytes per candidate.
+ *             is (H / ckpt + b ckpt n_sub) x 320 bytes per candidate, b the
+ *             number of segment buffers: 2 while the grid of 16-candidate
+ *             CTAs fits the device in one wave (one set of warps then
+ *             recomputes the next segment while another walks this one
+ *             back), else 1.  The results are the same bits either way and
+ *             for every ckpt.
  * Four threads per candidate (one wheel each); F32X4 terrain only. */
 int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
              const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int K, int H, float dt,

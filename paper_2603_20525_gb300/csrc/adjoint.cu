@@ -12,15 +12,17 @@
 // exchanges only sums (the force and moment sums forwards; the wheels'
 // contributions to the body adjoints backwards).  The forward pass stores the
 // state every `ckpt` control steps; the reverse pass recomputes one segment
-// at a time into a per-lane buffer and walks its Euler steps backwards.  Each
-// backward step recomputes the step's intermediates from the stored state
-// and propagates the state adjoint lambda through the Euler update, the state
-// derivative A(xi) + B zeta, the force and moment sums, every wheel (contact
-// kinematics, bilinear terrain, suspension with liftoff, slip and tire), the
-// rotation and the running cost with its ESM soft constraint.  Branches
-// (spring and damper liftoff, steering clamps, off-map clamping, the goal
-// test) follow the forward pass's choice, so the result is the derivative of
-// the piecewise-smooth discrete map along the primal trajectory.
+// at a time into a per-lane buffer and walks its Euler steps backwards (for
+// a small grid on separate warps, the next segment recomputed while this one
+// is walked).  Each backward step recomputes the step's intermediates from
+// the stored state and propagates the state adjoint lambda through the Euler
+// update, the state derivative A(xi) + B zeta, the force and moment sums,
+// every wheel (contact kinematics, bilinear terrain, suspension with
+// liftoff, slip and tire), the rotation and the running cost with its ESM
+// soft constraint.  Branches (spring and damper liftoff, steering clamps,
+// off-map clamping, the goal test) follow the forward pass's choice, so the
+// result is the derivative of the piecewise-smooth discrete map along the
+// primal trajectory.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -554,140 +556,184 @@ __device__ __forceinline__ void esm_adj(const Veh &V, const St &s, float lam[13]
     lam[5] += a_sph * cph - a_cph * sph;
 }
 
-__global__ void __launch_bounds__(64, 1) grad_kernel(const __grid_constant__ GradParams p)
+// The forward pass stores the checkpoints and the last segment's Euler-step
+// start states.  Then round i walks segment n_seg - 1 - i backwards and
+// recomputes the segment before it.
+//   SPLIT = false: one quad per candidate walks, then recomputes into the
+//   buffer it has just read (one buffer).
+//   SPLIT = true (a grid that leaves most of the GPU idle): each CTA holds
+//   its kGradCands candidates twice.  Its first half of threads walks, its
+//   second half recomputes, both having run the forward pass (the same
+//   bits), so the recomputation runs beside the walk instead of before it,
+//   into the other of two buffers.  A CTA barrier ends each round; every
+//   thread, a candidate-less one included, passes the same number of
+//   barriers (n_seg, uniform over the grid).
+template <bool SPLIT>
+__global__ void __launch_bounds__(SPLIT ? 2 * kGradHalf : kGradHalf, 1) grad_kernel(const __grid_constant__ GradParams p)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool walker = !SPLIT || threadIdx.x < kGradHalf;
+    const bool recomp = !SPLIT || !walker;
+    const int tid = blockIdx.x * kGradHalf + (threadIdx.x & (kGradHalf - 1));   // lane slot, either half
     const int j = tid / kGradLanes;
-    if (j >= p.K) return;                       // whole quads leave together
+    const bool active = j < p.K;                // whole quads, in both halves alike
     const Lane ln = lane_of(p.V, tid & (kGradLanes - 1), 0xfu << (threadIdx.x & 28));
     const Terrain &T = p.T;
     const Cost &Cc = p.C;
     const size_t K = (size_t)p.K;
     const size_t KL = K * kGradLanes;           // every lane keeps its own copy of the states
-    St s;
-    {
-        float q[13];
-        if (p.x0_soa) {
-#pragma unroll
-            for (int c = 0; c < 13; ++c) q[c] = p.x0_soa[c * K + j];
-        } else {
-#pragma unroll
-            for (int c = 0; c < 13; ++c) q[c] = p.x0[c];
-        }
-        two_sum(q[0], -T.x0_hi, s.x, s.xl);
-        s.xl -= T.x0_lo;
-        two_sum(q[1], -T.y0_hi, s.y, s.yl);
-        s.yl -= T.y0_lo;
-        s.z = q[2]; s.psi = q[3]; s.th = q[4]; s.ph = q[5];
-        s.vx = q[6]; s.vy = q[7]; s.vz = q[8];
-        s.wx = q[9]; s.wy = q[10]; s.wz = q[11]; s.d = q[12];
-        s.zl = s.psil = s.vxl = s.vyl = s.vzl = 0.f;
-    }
     const int n_seg = (p.H + p.ckpt - 1) / p.ckpt;
-    float *ck = p.ckpt_buf + tid;                 // [n_seg][20][K lanes]
-    float *seg = p.seg_buf + tid;                 // [ckpt * n_sub][20][K lanes]
-    // forward: cost (or margin) and checkpoints
+    const int k_last = (n_seg - 1) * p.ckpt;    // first control step of the last segment
+    const size_t seg_stride = (size_t)p.ckpt * p.n_sub * kStFloats * KL;
+    float *ck = p.ckpt_buf + tid;               // [n_seg][20][K lanes]
+    float *seg = p.seg_buf + tid;               // [2][ckpt * n_sub][20][K lanes]
     const bool want_margin = p.objective == kGradMargin;
+    St s;
     float J = 0.f;
     float Umin = CUDART_INF_F;                   // the margin: min U_ESM over the states
     int emin = 0;                                // index of the state holding it (first on ties)
-    bool done = false;
     int done_step = p.H * p.n_sub;               // Euler step index where the goal stopped the rollout
-    for (int k = 0; k < p.H; ++k) {
-        if (k % p.ckpt == 0) st_store(ck + (size_t)(k / p.ckpt) * kStFloats * KL, KL, s);
-        const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
-        const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
-        for (int q = 0; q < p.n_sub && !done; ++q) {
-            if (want_margin) {
-                const float U = state_esm(p.V, s);
-                if (U < Umin) {
-                    Umin = U;
-                    emin = k * p.n_sub + q;
-                }
-            }
-            const StepOut o = step_fwd(p, s, dd, u.y, ln);
-            if (!o.stepped) {
-                done = true;
-                done_step = k * p.n_sub + q;
-                break;
-            }
-            J = fmaf(p.h, o.L, J);
-        }
-    }
-    // terminal cost and its gradient, or the final state's share of the margin
     float lam[13];
 #pragma unroll
     for (int c = 0; c < 13; ++c) lam[c] = 0.f;
-    if (want_margin) {
-        const int e_final = done ? done_step : p.H * p.n_sub;
-        const float U = state_esm(p.V, s);
-        if (U < Umin) {
-            Umin = U;
-            emin = e_final;
+    if (active) {
+        {
+            float q[13];
+            if (p.x0_soa) {
+#pragma unroll
+                for (int c = 0; c < 13; ++c) q[c] = p.x0_soa[c * K + j];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 13; ++c) q[c] = p.x0[c];
+            }
+            two_sum(q[0], -T.x0_hi, s.x, s.xl);
+            s.xl -= T.x0_lo;
+            two_sum(q[1], -T.y0_hi, s.y, s.yl);
+            s.yl -= T.y0_lo;
+            s.z = q[2]; s.psi = q[3]; s.th = q[4]; s.ph = q[5];
+            s.vx = q[6]; s.vy = q[7]; s.vz = q[8];
+            s.wx = q[9]; s.wy = q[10]; s.wz = q[11]; s.d = q[12];
+            s.zl = s.psil = s.vxl = s.vyl = s.vzl = 0.f;
         }
-        if (emin == e_final) esm_adj(p.V, s, lam);
-        if (ln.q == 0) p.cost[j] = Umin;
-    } else {
-        const float gdx = (s.x - Cc.gx_hi) + (s.xl - Cc.gx_lo);
-        const float gdy = (s.y - Cc.gy_hi) + (s.yl - Cc.gy_lo);
-        const float dist = sqrtf(fmaf(gdx, gdx, gdy * gdy));
-        J = fmaf(Cc.wg, dist, J);
-        if (ln.q == 0) p.cost[j] = J;
-        if (dist > 0.f) {
-            lam[0] = Cc.wg * gdx / dist;
-            lam[1] = Cc.wg * gdy / dist;
+        // forward: cost (or margin), checkpoints and the last segment's states
+        bool done = false;
+        for (int k = 0; k < p.H; ++k) {
+            if (recomp && k % p.ckpt == 0) st_store(ck + (size_t)(k / p.ckpt) * kStFloats * KL, KL, s);
+            const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
+            const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
+            for (int q = 0; q < p.n_sub && !done; ++q) {
+                if (recomp && k >= k_last)
+                    st_store(seg + (size_t)((k - k_last) * p.n_sub + q) * kStFloats * KL, KL, s);
+                if (want_margin) {
+                    const float U = state_esm(p.V, s);
+                    if (U < Umin) {
+                        Umin = U;
+                        emin = k * p.n_sub + q;
+                    }
+                }
+                const StepOut o = step_fwd(p, s, dd, u.y, ln);
+                if (!o.stepped) {
+                    done = true;
+                    done_step = k * p.n_sub + q;
+                    break;
+                }
+                J = fmaf(p.h, o.L, J);
+            }
+        }
+        // terminal cost and its gradient, or the final state's share of the margin
+        if (walker) {
+            if (want_margin) {
+                const int e_final = done ? done_step : p.H * p.n_sub;
+                const float U = state_esm(p.V, s);
+                if (U < Umin) {
+                    Umin = U;
+                    emin = e_final;
+                }
+                if (emin == e_final) esm_adj(p.V, s, lam);
+                if (ln.q == 0) p.cost[j] = Umin;
+            } else {
+                const float gdx = (s.x - Cc.gx_hi) + (s.xl - Cc.gx_lo);
+                const float gdy = (s.y - Cc.gy_hi) + (s.yl - Cc.gy_lo);
+                const float dist = sqrtf(fmaf(gdx, gdx, gdy * gdy));
+                J = fmaf(Cc.wg, dist, J);
+                if (ln.q == 0) p.cost[j] = J;
+                if (dist > 0.f) {
+                    lam[0] = Cc.wg * gdx / dist;
+                    lam[1] = Cc.wg * gdy / dist;
+                }
+            }
         }
     }
-    // reverse, one checkpointed segment at a time
-    for (int sg = n_seg - 1; sg >= 0; --sg) {
-        const int k0 = sg * p.ckpt, k1 = min(p.H, k0 + p.ckpt);
-        St r;
-        st_load(ck + (size_t)sg * kStFloats * KL, KL, r);
-        // recompute the segment's Euler-step start states
-        int n_steps = 0;
-        for (int k = k0; k < k1; ++k) {
-            const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
-            const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
-            for (int q = 0; q < p.n_sub; ++q) {
-                const int e = k * p.n_sub + q;
-                if (e >= done_step) break;
-                st_store(seg + (size_t)n_steps * kStFloats * KL, KL, r);
-                ++n_steps;
-                step_fwd(p, r, dd, u.y, ln);
+    if (SPLIT) __syncthreads();                 // the last segment's states are stored
+    // reverse: round i walks segment n_seg - 1 - i and recomputes the one before it
+    for (int i = 0; i < n_seg; ++i) {
+        const int sw = n_seg - 1 - i;
+        if (active && walker) {
+            const int k0 = sw * p.ckpt, k1 = min(p.H, k0 + p.ckpt);
+            const float *buf = SPLIT ? seg + (size_t)(i & 1) * seg_stride : seg;
+            for (int k = k1 - 1; k >= k0; --k) {
+                const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
+                const bool inside = !(u.x < -p.V.ddmax || u.x > p.V.ddmax);   // as the clamp
+                const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
+                float g_dd = 0.f, g_ax = 0.f;
+                for (int q = p.n_sub - 1; q >= 0; --q) {
+                    const int e = k * p.n_sub + q;
+                    if (e >= done_step) continue;
+                    St r2;
+                    st_load(buf + (size_t)(e - k0 * p.n_sub) * kStFloats * KL, KL, r2);
+                    step_adj(p, r2, dd, u.y, lam, g_dd, g_ax, ln);
+                    // lam is now the adjoint of the step's start state
+                    if (want_margin && e == emin) esm_adj(p.V, r2, lam);
+                }
+                // the steering rate is clamped to +/- its limit before use
+                if (ln.q == 0) {
+                    p.grad[((size_t)k * K + j) * 2] = inside ? g_dd : 0.f;
+                    p.grad[((size_t)k * K + j) * 2 + 1] = g_ax;
+                }
             }
         }
-        // walk the segment's steps backwards
-        for (int k = k1 - 1; k >= k0; --k) {
-            const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
-            const bool inside = !(u.x < -p.V.ddmax || u.x > p.V.ddmax);   // as the clamp
-            const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
-            float g_dd = 0.f, g_ax = 0.f;
-            for (int q = p.n_sub - 1; q >= 0; --q) {
-                const int e = k * p.n_sub + q;
-                if (e >= done_step) continue;
-                const int local = e - k0 * p.n_sub;
-                St r2;
-                st_load(seg + (size_t)local * kStFloats * KL, KL, r2);
-                step_adj(p, r2, dd, u.y, lam, g_dd, g_ax, ln);
-                // lam is now the adjoint of the step's start state
-                if (want_margin && e == emin) esm_adj(p.V, r2, lam);
-            }
-            // the steering rate is clamped to +/- its limit before use
-            if (ln.q == 0) {
-                p.grad[((size_t)k * K + j) * 2] = inside ? g_dd : 0.f;
-                p.grad[((size_t)k * K + j) * 2 + 1] = g_ax;
+        if (active && recomp && sw > 0) {
+            // recompute segment sw - 1's Euler-step start states
+            const int sr = sw - 1;
+            const int k0 = sr * p.ckpt, k1 = k0 + p.ckpt;                 // never the last segment
+            float *buf = SPLIT ? seg + (size_t)((i + 1) & 1) * seg_stride : seg;
+            St r;
+            st_load(ck + (size_t)sr * kStFloats * KL, KL, r);
+            int n_steps = 0;
+            for (int k = k0; k < k1; ++k) {
+                const float2 u = __ldg(p.ctrl + (size_t)k * K + j);
+                const float dd = clampf(u.x, -p.V.ddmax, p.V.ddmax);
+                for (int q = 0; q < p.n_sub; ++q) {
+                    const int e = k * p.n_sub + q;
+                    if (e >= done_step) break;
+                    st_store(buf + (size_t)n_steps * kStFloats * KL, KL, r);
+                    ++n_steps;
+                    step_fwd(p, r, dd, u.y, ln);
+                }
             }
         }
-        (void)n_steps;
+        if (SPLIT && i + 1 < n_seg) __syncthreads();   // segment sw - 1 is stored; segment sw is read
     }
 }
 
 }  // namespace
 
+int grad_split_ctas(int device)
+{
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_kernel<true>, 2 * kGradHalf, 0) !=
+        cudaSuccess)
+        return 0;
+    return sms * per_sm;
+}
+
 cudaError_t launch_grad(const GradParams &p, cudaStream_t stream)
 {
-    const size_t threads = (size_t)p.K * kGradLanes;
-    grad_kernel<<<(unsigned)((threads + 63) / 64), 64, 0, stream>>>(p);
+    const unsigned blocks = (unsigned)((p.K + kGradCands - 1) / kGradCands);
+    if (p.split)
+        grad_kernel<true><<<blocks, 2 * kGradHalf, 0, stream>>>(p);
+    else
+        grad_kernel<false><<<blocks, kGradHalf, 0, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,7 @@ struct atp_ctx {
     size_t scratch_bytes;
     atp::BatchParams *batch;  // host staging of one batch's descriptors
     float4 *cm_box;           // the costmap's per-perimeter reach boxes (device)
+    int grad_ctas;            // resident CTAs of the split adjoint layout, -1 until queried
 };
 
 namespace {
@@ -332,6 +333,7 @@ int atp_create(atp_ctx **out, int device)
     ctx->acc64 = 0;
     ctx->lanes = 0;
     ctx->stage = 0;
+    ctx->grad_ctas = -1;
     ctx->err[0] = 0;
     ctx->batch = new (std::nothrow) atp::BatchParams;
     if (!ctx->batch) {
@@ -760,9 +762,12 @@ int grad_impl(atp_ctx *ctx, int objective, const atp_vehicle *veh, const atp_cos
     const size_t n_seg = (size_t)(H + ckpt - 1) / ckpt;
     const size_t KL = (size_t)K * atp::kGradLanes;      // every lane keeps its own states
     const size_t ck_bytes = align_up(n_seg * 20 * KL * sizeof(float));
-    const size_t seg_bytes = align_up((size_t)ckpt * ns * 20 * KL * sizeof(float));
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(ctx, g.err, "set device");
+    if (ctx->grad_ctas < 0) ctx->grad_ctas = atp::grad_split_ctas(ctx->device);
+    // walking and recomputing on separate warps pays while one wave holds the grid
+    const bool split = ((size_t)K + atp::kGradCands - 1) / atp::kGradCands <= (size_t)ctx->grad_ctas;
+    const size_t seg_bytes = align_up((split ? 2 : 1) * (size_t)ckpt * ns * 20 * KL * sizeof(float));
     if ((rc = ensure_scratch_bytes(ctx, ck_bytes + seg_bytes)) != ATP_OK) return rc;
     char *base = (char *)ctx->scratch + kHeaderBytes;
     atp::PlanParams pp;
@@ -783,6 +788,7 @@ int grad_impl(atp_ctx *ctx, int objective, const atp_vehicle *veh, const atp_cos
     p.ckpt = ckpt;
     p.h = pp.h;
     p.objective = objective;
+    p.split = split;
     p.cost = cost_dev;
     p.grad = grad_dev;
     p.ckpt_buf = (float *)base;

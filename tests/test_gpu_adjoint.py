@@ -91,6 +91,33 @@ def test_checkpoint_interval_does_not_change_the_result(setup):
     assert np.array_equal(G1, G10) and np.array_equal(G10, G100)
 
 
+
+@pytest.mark.parametrize("objective", ["cost", "margin"])
+@pytest.mark.parametrize("ckpt", [10, 7])
+def test_every_layout_same_bits(setup, objective, ckpt):
+    """A small grid walks and recomputes on separate warps, a grid beyond
+    one wave on the same quad; a CTA short of candidates leaves quads idle.
+    The top-64's gradients, alone (split), as the first 50 (idle quads) and
+    as 256 copies in a batch of 16384 (one quad per candidate), are the same
+    bits, for a checkpoint interval that divides H and one that does not."""
+    w = setup["w"]
+    x0 = [float(v) for v in w.x0]
+
+    def grad(ctrl):
+        c = torch.as_tensor(np.ascontiguousarray(ctrl)).cuda()
+        J, G = setup["ctx"].grad(w.vehicle, w.cost, setup["ter"], x0, c, w.dt, w.n_sub, ckpt,
+                                 objective=objective)
+        torch.cuda.synchronize()
+        return J.cpu().numpy(), G.cpu().numpy()
+
+    c64 = setup["ctrl"]
+    J, G = grad(c64)
+    J50, G50 = grad(c64[:, :50])
+    assert J50.tobytes() == J[:50].tobytes() and G50.tobytes() == G[:, :50].tobytes()
+    Jb, Gb = grad(np.tile(c64, (1, 256, 1)))
+    assert Jb.tobytes() == np.tile(J, 256).tobytes()
+    assert Gb.tobytes() == np.tile(G, (1, 256, 1)).tobytes()
+
 def test_autograd_function_and_refinement(setup):
     from paper_2603_20525_gb300.autograd import RolloutCost, refine
     s = setup
