@@ -23,10 +23,11 @@ namespace atp {
 namespace {
 
 constexpr int kRowThreads = 256;  // row-pass CTA
-constexpr int kRowOut = 4;        // consecutive outputs per row-pass thread
+constexpr int kRowOut = 8;        // consecutive outputs per row-pass thread (a multiple of 4)
+constexpr int kRowVec = kRowOut / 4;
 constexpr int kRowTile = kRowThreads * kRowOut;   // outputs per row-pass CTA
-constexpr int kColTile = 64;      // rows per column-pass CTA (32 columns wide)
-constexpr int kColOut = 8;        // consecutive rows per column-pass thread
+constexpr int kColOut = 16;       // consecutive rows per column-pass thread
+constexpr int kColTile = 8 * kColOut;             // rows per column-pass CTA (32 columns wide)
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -65,8 +66,8 @@ __device__ void gauss_weights(float *w, int r, float inv2s2)
 }
 
 // out[j][i] = sum_k w[k] in[j][clamp(i + k - r)], each sum over k in order.
-// Thread t makes outputs 4t .. 4t+3 of the CTA's 1024 from a window of eight
-// tile values refilled by one 16-byte shared load per four taps.
+// Thread t makes outputs 8t .. 8t+7 of the CTA's 2048 from a window of
+// twelve tile values refilled by one 16-byte shared load per four taps.
 __global__ void __launch_bounds__(kRowThreads) lod_rows_kernel(LodParams p)
 {
     extern __shared__ __align__(16) float sm[];         // the tile is read as float4
@@ -82,36 +83,45 @@ __global__ void __launch_bounds__(kRowThreads) lod_rows_kernel(LodParams p)
     __syncthreads();
     const int ib = i0 + kRowOut * threadIdx.x;
     if (ib >= p.nx) return;
-    const float4 *t4 = reinterpret_cast<const float4 *>(tile) + threadIdx.x;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    float4 lo = t4[0];
+    const float4 *t4 = reinterpret_cast<const float4 *>(tile) + kRowVec * threadIdx.x;
+    float acc[kRowOut];
+    float4 win[kRowVec + 1];
+#pragma unroll
+    for (int q = 0; q < kRowOut; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int c = 0; c < kRowVec; ++c) win[c] = t4[c];
     const int n = 2 * p.r + 1;
     for (int k0 = 0; k0 < n; k0 += 4) {
-        const float4 hi = t4[(k0 >> 2) + 1];
-        const float v[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+        win[kRowVec] = t4[(k0 >> 2) + kRowVec];
+        float v[kRowOut + 4];
+#pragma unroll
+        for (int c = 0; c <= kRowVec; ++c) {
+            v[4 * c] = win[c].x;
+            v[4 * c + 1] = win[c].y;
+            v[4 * c + 2] = win[c].z;
+            v[4 * c + 3] = win[c].w;
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             if (k0 + e < n) {
                 const float wk = w[k0 + e];
-                a0 = fmaf(wk, v[e], a0);
-                a1 = fmaf(wk, v[e + 1], a1);
-                a2 = fmaf(wk, v[e + 2], a2);
-                a3 = fmaf(wk, v[e + 3], a3);
+#pragma unroll
+                for (int q = 0; q < kRowOut; ++q) acc[q] = fmaf(wk, v[e + q], acc[q]);
             }
         }
-        lo = hi;
+#pragma unroll
+        for (int c = 0; c < kRowVec; ++c) win[c] = win[c + 1];
     }
     float *o = p.out + (size_t)j * p.nx + ib;
-    o[0] = a0;
-    if (ib + 1 < p.nx) o[1] = a1;
-    if (ib + 2 < p.nx) o[2] = a2;
-    if (ib + 3 < p.nx) o[3] = a3;
+#pragma unroll
+    for (int q = 0; q < kRowOut; ++q)
+        if (ib + q < p.nx) o[q] = acc[q];
 }
 
 // out[j][i] = sum_k w[k] in[clamp(j + k - r)][i], each sum over k in order; a
-// CTA of 32 x 8 threads covers 32 columns and kColTile rows, thread (x, y)
-// rows 8y .. 8y+7 of column x from a window of sixteen tile rows refilled
-// with eight loads per eight taps.
+// CTA of 32 x 8 threads covers 32 columns and kColTile = 128 rows, thread
+// (x, y) rows 16y .. 16y+15 of column x from a window of 32 tile rows
+// refilled with sixteen loads per sixteen taps.
 __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
 {
     extern __shared__ float sm[];
@@ -121,7 +131,7 @@ __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j0 = blockIdx.y * kColTile;
     const int ic = min(i, p.nx - 1);
-    const int n_rows = kColTile + 2 * p.r + 8;
+    const int n_rows = kColTile + 2 * p.r + kColOut;
     for (int t = threadIdx.y; t < n_rows; t += 8)
         tile[t * 32 + threadIdx.x] = __ldg(p.in + (size_t)clampi(j0 - p.r + t, 0, p.ny - 1) * p.nx + ic);
     __syncthreads();
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
 size_t rows_smem(int r) { return sizeof(float) * (size_t)(((2 * r + 1 + 3) & ~3) + kRowTile + 2 * r + 8); }
 size_t cols_smem(int r)
 {
-    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (kColTile + 2 * r + 8) * 32);
+    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (kColTile + 2 * r + kColOut) * 32);
 }
 
 }  // namespace
