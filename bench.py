@@ -64,16 +64,20 @@ def fp32_peak_tflops(sms, mhz):
     return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
+# what the plan kernel is compiled from: its translation unit, the headers it
+# includes and the module that holds the compile flags
+PLAN_KERNEL_SOURCES = ("paper_2603_20525_gb300/csrc/plan_kernel.cu", "paper_2603_20525_gb300/csrc/plan_kernel.cuh",
+                       "paper_2603_20525_gb300/csrc/plan_tail.cuh", "paper_2603_20525_gb300/csrc/srb_model.cuh",
+                       "paper_2603_20525_gb300/csrc/fastmath.cuh", "include/atp.h",
+                       "paper_2603_20525_gb300/build.py")
+
+
 def kernel_sources_sha256():
-    import glob
+    """SHA-256 of the plan kernel's sources, in the order listed."""
     import hashlib
-    srcs = sorted(glob.glob(os.path.join(ROOT, "paper_2603_20525_gb300", "csrc", "*.cu")) +
-                  glob.glob(os.path.join(ROOT, "paper_2603_20525_gb300", "csrc", "*.cuh")) +
-                  [os.path.join(ROOT, "include", "atp.h")])
-    srcs = sorted(srcs, key=lambda p: os.path.relpath(p, ROOT))
     h = hashlib.sha256()
-    for p in srcs:
-        with open(p, "rb") as f:
+    for rel in PLAN_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 

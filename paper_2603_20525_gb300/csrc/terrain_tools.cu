@@ -23,11 +23,13 @@ namespace atp {
 namespace {
 
 constexpr int kRowThreads = 256;  // row-pass CTA
-constexpr int kRowOut = 8;        // consecutive outputs per row-pass thread (a multiple of 4)
-constexpr int kRowVec = kRowOut / 4;
-constexpr int kRowTile = kRowThreads * kRowOut;   // outputs per row-pass CTA
-constexpr int kColOut = 16;       // consecutive rows per column-pass thread
-constexpr int kColTile = 8 * kColOut;             // rows per column-pass CTA (32 columns wide)
+// Outputs per thread: 4 row and 8 column outputs below this radius, 8 and 16
+// from it on.  Small radii are bound by each CTA's set-up, and more outputs
+// per thread only halve the CTAs; large radii by the taps, where the wider
+// windows load fewer values per output (measured on the GB300: the narrow
+// form 4 % faster at 12 cells, the wide one 5 % at 24 and 10 to 16 % at 36
+// to 200 cells; the same bits).
+constexpr int kLodWideMinR = 16;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -66,10 +68,14 @@ __device__ void gauss_weights(float *w, int r, float inv2s2)
 }
 
 // out[j][i] = sum_k w[k] in[j][clamp(i + k - r)], each sum over k in order.
-// Thread t makes outputs 8t .. 8t+7 of the CTA's 2048 from a window of
-// twelve tile values refilled by one 16-byte shared load per four taps.
+// Thread t makes outputs OUT t .. OUT t + OUT - 1 of the CTA's 256 OUT from a
+// window of OUT + 4 tile values refilled by one 16-byte shared load per four
+// taps.
+template <int OUT>
 __global__ void __launch_bounds__(kRowThreads) lod_rows_kernel(LodParams p)
 {
+    static_assert(OUT % 4 == 0, "whole float4 windows");
+    constexpr int kRowOut = OUT, kRowVec = OUT / 4, kRowTile = kRowThreads * OUT;
     extern __shared__ __align__(16) float sm[];         // the tile is read as float4
     float *w = sm;                                      // 2r + 1, padded to 4
     float *tile = sm + ((2 * p.r + 1 + 3) & ~3);        // kRowTile + 2r + 8
@@ -119,11 +125,13 @@ __global__ void __launch_bounds__(kRowThreads) lod_rows_kernel(LodParams p)
 }
 
 // out[j][i] = sum_k w[k] in[clamp(j + k - r)][i], each sum over k in order; a
-// CTA of 32 x 8 threads covers 32 columns and kColTile = 128 rows, thread
-// (x, y) rows 16y .. 16y+15 of column x from a window of 32 tile rows
-// refilled with sixteen loads per sixteen taps.
+// CTA of 32 x 8 threads covers 32 columns and 8 OUT rows, thread (x, y) rows
+// OUT y .. OUT y + OUT - 1 of column x from a window of 2 OUT tile rows
+// refilled with OUT loads per OUT taps.
+template <int OUT>
 __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
 {
+    constexpr int kColOut = OUT, kColTile = 8 * OUT;
     extern __shared__ float sm[];
     float *w = sm;                           // 2r + 1, padded to a multiple of 32
     float *tile = sm + ((2 * p.r + 1 + 31) & ~31);   // [kColTile + 2r + 8][32]
@@ -167,10 +175,37 @@ __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
     }
 }
 
-size_t rows_smem(int r) { return sizeof(float) * (size_t)(((2 * r + 1 + 3) & ~3) + kRowTile + 2 * r + 8); }
-size_t cols_smem(int r)
+size_t rows_smem(int r, int out)
 {
-    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (kColTile + 2 * r + kColOut) * 32);
+    return sizeof(float) * (size_t)(((2 * r + 1 + 3) & ~3) + kRowThreads * out + 2 * r + 8);
+}
+size_t cols_smem(int r, int out)
+{
+    return sizeof(float) * (size_t)(((2 * r + 1 + 31) & ~31) + (8 * out + 2 * r + out) * 32);
+}
+
+template <int ROW_OUT, int COL_OUT>
+cudaError_t lod_passes(LodParams p, float *tmp, float *out, cudaStream_t stream)
+{
+    const int r = p.r;
+    cudaError_t e = cudaFuncSetAttribute(lod_rows_kernel<ROW_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rows_smem(kLodMaxRadius, ROW_OUT));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(lod_cols_kernel<COL_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cols_smem(kLodMaxRadius, COL_OUT));
+    if (e != cudaSuccess) return e;
+    p.out = tmp;
+    const int row_tile = kRowThreads * ROW_OUT;
+    lod_rows_kernel<ROW_OUT><<<dim3((unsigned)((p.nx + row_tile - 1) / row_tile), (unsigned)p.ny), kRowThreads,
+                               rows_smem(r, ROW_OUT), stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    p.in = tmp;
+    p.out = out;
+    const int col_tile = 8 * COL_OUT;
+    lod_cols_kernel<COL_OUT><<<dim3((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny + col_tile - 1) / col_tile)),
+                               dim3(32, 8), cols_smem(r, COL_OUT), stream>>>(p);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -179,28 +214,13 @@ cudaError_t launch_lod_smooth(const float *in, float *tmp, float *out, int nx, i
                               float inv2s2, cudaStream_t stream)
 {
     if (r < 0 || r > kLodMaxRadius) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(lod_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rows_smem(kLodMaxRadius));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(lod_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)cols_smem(kLodMaxRadius));
-    if (e != cudaSuccess) return e;
     LodParams p;
     p.nx = nx;
     p.ny = ny;
     p.r = r;
     p.inv2s2 = inv2s2;
     p.in = in;
-    p.out = tmp;
-    lod_rows_kernel<<<dim3((unsigned)((nx + kRowTile - 1) / kRowTile), (unsigned)ny), kRowThreads,
-                      rows_smem(r), stream>>>(p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    p.in = tmp;
-    p.out = out;
-    lod_cols_kernel<<<dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + kColTile - 1) / kColTile)),
-                      dim3(32, 8), cols_smem(r), stream>>>(p);
-    return cudaGetLastError();
+    return r < kLodWideMinR ? lod_passes<4, 8>(p, tmp, out, stream) : lod_passes<8, 16>(p, tmp, out, stream);
 }
 
 // ---------------------------------------------------------------------------
