@@ -227,8 +227,10 @@ int atp_terrain_prepare(atp_ctx *ctx, const float *heights_dev, const float *cos
  *   cand_flags_dev uint8 [N] or NULL: ATP_FLAG_* bits
  *   cand_xf_dev   float [13][N] or NULL: final states, SoA
  *   stream        cudaStream_t
- * 1 <= N <= 2^31 - 1, H >= 1, dt > 0, 0 <= n_sub.  Validation failures return
- * ATP_ERR_INVALID; launch failures ATP_ERR_CUDA. */
+ * 1 <= N, H >= 1, dt > 0, 0 <= n_sub.  Validation failures return
+ * ATP_ERR_INVALID; N above 2^31 - 1025 (the most candidates any call takes, so
+ * that every kernel's thread index stays within 32 bits) ATP_ERR_UNSUPPORTED;
+ * launch failures ATP_ERR_CUDA. */
 int atp_plan(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
              const atp_terrain *terrain, const atp_state *x0, const float *x0_dev,
              const float *ctrl_dev, int N, int H, float dt, int n_sub,
@@ -295,7 +297,8 @@ int atp_plan_batch(atp_ctx *ctx, const atp_plan_request *reqs, int n_req, void *
  *             recomputes the next segment while another walks this one
  *             back), else 1.  The results are the same bits either way and
  *             for every ckpt.
- * Four threads per candidate (one wheel each); F32X4 terrain only. */
+ * Four threads per candidate (one wheel each); K <= 2^28; F32X4 terrain
+ * only. */
 int atp_grad(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *terrain,
              const atp_state *x0, const float *x0_dev, const float *ctrl_dev, int K, int H, float dt,
              int n_sub, int ckpt, float *cost_dev, float *grad_dev, void *stream);
@@ -323,7 +326,7 @@ int atp_grad_margin(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost,
  *                      than cost: ctrl, grad and cost take the trial's and
  *                      eta grows by 1.5; for the others eta halves.
  * An iteration is trial, atp_grad on the trial, accept; the cost then never
- * increases.  K, H >= 1; step > 0; rate_max >= 0. */
+ * increases.  K, H >= 1, K <= 2^31 - 1025; step > 0; rate_max >= 0. */
 int atp_refine_init(atp_ctx *ctx, const float *grad_dev, int K, int H, float step, float *eta_dev, void *stream);
 int atp_refine_trial(atp_ctx *ctx, const float *ctrl_dev, const float *grad_dev, const float *eta_dev, int K,
                      int H, float rate_max, float *trial_dev, void *stream);
@@ -341,7 +344,7 @@ int atp_refine_accept(atp_ctx *ctx, int K, int H, const float *trial_dev, const 
  * The nominal is a warm start from the previous plan's best controls,
  * nominal[k] = prev_best[min(k + shift, H_prev - 1)] (float [H_prev][2],
  * device), or zero when H_prev = 0.  Draws depend only on (key, nonce, j, k),
- * not on the launch.  1 <= H <= 65535. */
+ * not on the launch.  1 <= H <= 65535, 1 <= N <= 2^31 - 1025. */
 int atp_sample(atp_ctx *ctx, const float *prev_best_dev, int H_prev, int shift, double sigma_rate,
                double sigma_acc, uint64_t key0, uint64_t key1, uint64_t nonce, int N, int H,
                float *ctrl_dev, void *stream);

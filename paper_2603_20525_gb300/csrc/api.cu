@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -247,6 +248,10 @@ void derive(const atp_vehicle &v, const atp_cost &c, const atp_terrain &t, atp::
     split(t.y0, T.y0_hi, T.y0_lo);
 }
 
+// The most candidates of one call: every kernel's 32-bit thread index over
+// one-thread-per-candidate grids, rounded up to its block, stays below 2^31.
+constexpr int kMaxN = INT_MAX - 1024;
+
 int common_checks(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, const atp_terrain *ter,
                   const float *x0, int n_state, const float *x0_dev, const float *ctrl_dev, int N,
                   int H, float dt, int n_sub, int *n_sub_out)
@@ -263,6 +268,7 @@ int common_checks(atp_ctx *ctx, const atp_vehicle *veh, const atp_cost *cost, co
     if (!ctrl_dev) return fail(ctx, ATP_ERR_INVALID, "ctrl_dev is NULL");
     if ((uintptr_t)ctrl_dev % 8 != 0) return fail(ctx, ATP_ERR_INVALID, "ctrl_dev must be 8-byte aligned");
     if (N < 1) return fail(ctx, ATP_ERR_INVALID, "N must be >= 1");
+    if (N > kMaxN) return fail(ctx, ATP_ERR_UNSUPPORTED, "N above %d", kMaxN);
     if (H < 1) return fail(ctx, ATP_ERR_INVALID, "H must be >= 1");
     if (!(dt > 0.f) || !std::isfinite(dt)) return fail(ctx, ATP_ERR_INVALID, "dt must be finite and > 0");
     if (n_sub < 0 || n_sub > 1000000) return fail(ctx, ATP_ERR_INVALID, "n_sub must be in [0, 1e6]");
@@ -755,6 +761,8 @@ int grad_impl(atp_ctx *ctx, int objective, const atp_vehicle *veh, const atp_cos
     if (rc != ATP_OK) return rc;
     if (terrain->format != ATP_TERRAIN_F32X4)
         return fail(ctx, ATP_ERR_UNSUPPORTED, "the adjoint takes F32X4 terrain only");
+    // four lanes per candidate, up to twice in a CTA: the lane slot stays within 32 bits
+    if (K > (1 << 28)) return fail(ctx, ATP_ERR_UNSUPPORTED, "the adjoint takes at most 2^28 candidates");
     if (!cost_dev || !grad_dev) return fail(ctx, ATP_ERR_INVALID, "cost_dev and grad_dev are required");
     if (ckpt == 0) ckpt = 10;
     if (ckpt < 1) return fail(ctx, ATP_ERR_INVALID, "ckpt must be >= 1 (0 selects 10)");
@@ -825,6 +833,7 @@ bool al8(const void *p) { return (uintptr_t)p % 8 == 0; }
 int refine_checks(atp_ctx *ctx, int K, int H)
 {
     if (K < 1 || H < 1) return fail(ctx, ATP_ERR_INVALID, "need K >= 1 and H >= 1");
+    if (K > kMaxN) return fail(ctx, ATP_ERR_UNSUPPORTED, "K above %d", kMaxN);
     return ATP_OK;
 }
 
@@ -889,6 +898,7 @@ extern "C" int atp_sample(atp_ctx *ctx, const float *prev_best_dev, int H_prev, 
     if (!ctrl_dev || (uintptr_t)ctrl_dev % 8 != 0)
         return fail(ctx, ATP_ERR_INVALID, "ctrl_dev must be non-NULL and 8-byte aligned");
     if (N < 1 || H < 1 || H > 65535) return fail(ctx, ATP_ERR_INVALID, "need N >= 1 and 1 <= H <= 65535");
+    if (N > kMaxN) return fail(ctx, ATP_ERR_UNSUPPORTED, "N above %d", kMaxN);
     if (H_prev < 0 || shift < 0) return fail(ctx, ATP_ERR_INVALID, "H_prev and shift must be >= 0");
     if (H_prev > 0 && (!prev_best_dev || (uintptr_t)prev_best_dev % 8 != 0))
         return fail(ctx, ATP_ERR_INVALID, "prev_best_dev must be non-NULL and 8-byte aligned");

@@ -49,13 +49,17 @@ def test_lod_matches_oracle(ctx, cell, sigma):
         assert np.array_equal(g, f.astype(np.float64))
 
 
-def test_lod_ragged_and_small_maps(ctx):
-    for shape in ((1, 1), (3, 700), (700, 3), (65, 33)):
+@pytest.mark.parametrize("sigma", [0.3, 1.5])
+def test_lod_ragged_and_small_maps(ctx, sigma):
+    """Maps smaller than one CTA's tile and ragged against it, with the
+    narrow windows (r = 12 cells) and the wide ones (r = 60)."""
+    r = int(4 * sigma / 0.1 + 0.5)
+    for shape in ((1, 1), (3, 700), (700, 3), (65, 33), (129, 2049)):
         f = np.random.default_rng(1).normal(0, 1, shape).astype(np.float32)
-        g = ctx.lod_smooth(torch.as_tensor(f).cuda(), 0.1, 0.3)
+        g = ctx.lod_smooth(torch.as_tensor(f).cuda(), 0.1, sigma)
         torch.cuda.synchronize()
-        o = oracle.lod_smooth(f, 0.1, 0.3)
-        assert np.abs(g.cpu().numpy() - o).max() <= 2 * 28 * U * np.abs(f).max()
+        o = oracle.lod_smooth(f, 0.1, sigma)
+        assert np.abs(g.cpu().numpy() - o).max() <= 2 * (2 * r + 4) * U * np.abs(f).max()
 
 
 def test_lod_rejects_bad_arguments(ctx):
