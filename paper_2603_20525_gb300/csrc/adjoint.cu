@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(SPLIT ? 2 * kGradHalf : kGradHalf, 1) grad_ker
     const int k_last = (n_seg - 1) * p.ckpt;    // first control step of the last segment
     const size_t seg_stride = (size_t)p.ckpt * p.n_sub * kStFloats * KL;
     float *ck = p.ckpt_buf + tid;               // [n_seg][20][K lanes]
-    float *seg = p.seg_buf + tid;               // [2][ckpt * n_sub][20][K lanes]
+    float *seg = p.seg_buf + tid;               // [1 or 2][ckpt * n_sub][20][K lanes]
     const bool want_margin = p.objective == kGradMargin;
     St s;
     float J = 0.f;
