@@ -123,3 +123,26 @@ def test_flop_count_scales_with_the_horizon():
 
 def test_fp32_peak_from_unit_counts_and_clock():
     assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.54784) < 1e-9
+
+
+def test_traffic_record_holds_only_for_the_captured_plan_kernel(tmp_path, monkeypatch):
+    """The committed DRAM-traffic figure is reported while what the plan
+    kernel is compiled from still hashes to the captured value, and only for
+    the captured workload; a changed source drops it."""
+    for rel in bench.PLAN_KERNEL_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, rel)), rel
+    fake = tmp_path / "repo"                # a copy of the plan kernel's sources
+    for rel in bench.PLAN_KERNEL_SOURCES:
+        dst = fake / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    (fake / "profiles").mkdir()
+    (fake / "profiles" / "plan_kernel_traffic.txt").write_text(
+        "# a capture\nsources_sha256: %s\ndram_bytes_per_launch: 1234\nworkload: scaled\n"
+        % bench.kernel_sources_sha256())
+    assert bench.recorded_traffic("scaled") == 1234
+    assert bench.recorded_traffic("paper") is None
+    p = fake / "paper_2603_20525_gb300" / "csrc" / "srb_model.cuh"
+    p.write_bytes(p.read_bytes() + b"\n")
+    assert bench.recorded_traffic("scaled") is None
