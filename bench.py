@@ -672,10 +672,13 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
         }
-        if args.workload != "paper":
+        # the single-GPU characterisation (the paper configuration, the other
+        # kernels, the serving stream) runs at N = 1 only: under torchrun the
+        # other ranks would sit idle on their GPUs meanwhile
+        if args.workload != "paper" and ws == 1:
             line["paper_configuration"] = run_paper_config(ctx, dev, stream, flush, peak)
             line["other_kernels"] = run_variants(ctx, dev, stream, flush)
-        if args.serve_seconds > 0:
+        if args.serve_seconds > 0 and ws == 1:
             rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
             line["serving"] = run_serving(args.serve_seconds, local, rates, args.sweep_seconds)
         if not args.no_cpu_baseline and ws == 1:
