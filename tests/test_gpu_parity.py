@@ -73,12 +73,26 @@ def check_candidates(g, o, w, ctrl=None, x0=None):
     assert bad.size == 0, [(int(j), float(v["err"][j]), float(v["bound"][j])) for j in bad[:5]]
     assert v["stats"]["tail"] <= v["stats"]["cap"], v["stats"]
     assert v["stats"]["switch_misses"] <= v["stats"]["switch_cap"], v["stats"]
-    # all flag bits agree on the candidates that held the bound; the
-    # feasibility bit agrees on every candidate away from a switch
+    # the goal, off-map and non-finite bits agree on every candidate that
+    # held the bound
     ck = v["checked"]
-    assert np.array_equal(g["flags"][ck], o["flags"][ck])
-    sure = ~v["near"]
-    assert np.array_equal(g["flags"][sure] & 1, o["flags"][sure] & 1)
+    assert np.array_equal(g["flags"][ck] & 0xFE, o["flags"][ck] & 0xFE)
+    # the feasibility bit (feasible means min U > 0 and finite, Sec. IV-B)
+    # agrees on every candidate away from a switch whose FP32 reference stays
+    # in range.  Elsewhere FP32 arithmetic does not decide it, and either side
+    # is accepted, counted against the switch cap: at the U = 0 switch itself
+    # (for an angle within about 2.4e-4 rad of the tipping point 1 - sin
+    # rounds to 0 in FP32, while FP64 keeps a margin of order 1e-8), and on a
+    # wild candidate, one on which FP32 arithmetic itself (the reference on
+    # the same inputs) misses the oracle by more than the largest bound or
+    # ends finite where the oracle does not, or the other way round: a
+    # tumbling chassis that FP32 and FP64 follow down different paths.
+    fe_diff = (g["flags"] & 1) != (o["flags"] & 1)
+    sure = ~v["near"] & ~v["wild"]
+    assert not (sure & fe_diff).any(), np.nonzero(sure & fe_diff)[0][:5]
+    other_side = int((fe_diff & ~sure & ~v["flipped"]).sum())
+    print("feasibility decided the other way at a switch or on a wild candidate:", other_side)
+    assert v["stats"]["switch_misses"] + other_side <= v["stats"]["switch_cap"], (other_side, v["stats"])
     # over the workload, as accurate as FP32 arithmetic itself
     if v["stats"]["feasible"] >= 200:
         parity.assert_fp32_level(v["stats"])
@@ -202,23 +216,18 @@ def test_every_lane_layout_same_bits(ctx, case):
         assert outs[0]["best_idx"] == o["best_idx"]
 
 
-def test_paper_configuration_sampled(ctx):
+def test_paper_configuration_full_size(ctx):
     """The real-time configuration of Sec. IV-D at full size: 204,288
     candidates of 16 steps of 0.25 s (800 Euler steps of 5 ms), steering
     only, one thread per candidate.  The reduction is checked bit-exactly
-    over all GPU outputs; every output of 12000 sampled candidates, the
-    chosen one among them, against the oracle."""
+    over all GPU outputs, and every output of every candidate against the
+    oracle (about half of them tip over and end non-finite on both sides)."""
     w = gen.workload_paper(0)
     g = gpu_plan(ctx, w)
     assert g["best_idx"] == lexmin(g["cost"], g["flags"])
     assert g["n_feasible"] == int(np.count_nonzero(g["flags"] & 1))
     assert g["best_cost"] == g["cost"][g["best_idx"]]
-    rng = np.random.default_rng(1)
-    idx = np.unique(np.concatenate([rng.choice(w.N, 12000, replace=False), [g["best_idx"]]]))
-    ws = gen.Workload(w.name + "-sample", w.terrain, w.vehicle, w.cost, w.x0,
-                      np.ascontiguousarray(w.ctrl[:, idx]), w.dt, w.n_sub)
-    gs = {k: g[k][idx] for k in ("cost", "margin", "flags", "xf")}
-    check_candidates(gs, oracle_plan(ws), ws)
+    check_plan(g, oracle_plan(w), w)
 
 
 def test_rollout_equals_plan_outputs(ctx):
